@@ -1,0 +1,144 @@
+/*
+ * vet.h -- C ABI of libvet, a GB300 (sm_103a) implementation of the
+ * non-local Variable Eddington Tensor (VET) closure of VETTAM
+ * (Menon, Federrath, Krumholz, Kuiper, Wibking & Jung 2022, MNRAS;
+ * arXiv 2202.08778).
+ *
+ * The closure is the paper's Sec. 2.2.5 ("Computing the Eddington Tensor"):
+ *   1. solve the time-independent gray transfer equation
+ *        dI/ds = kappa (S - I)                                  (Eq. 14)
+ *      along a HEALPix set of N = 12 nside^2 directions (Sec. 2.2.5, App. B)
+ *      with hybrid characteristics (long characteristics inside cubic blocks,
+ *      bilinear interpolation of face intensities between blocks);
+ *   2. take the angular quadratures (Eqs. 6-8 and the discrete sums of
+ *      Sec. 2.2.5, with c = 1)
+ *        E = sum_k w_k I_k,  F_i = sum_k w_k I_k n_ik,
+ *        P_ij = sum_k w_k I_k n_ik n_jk,   w_k = 4 pi / N;
+ *   3. form the Eddington tensor f_ij = P_ij / E                (Eq. 9).
+ *
+ * Conventions shared by every entry point
+ *   - kappa is the absorption coefficient per unit length (the paper's
+ *     rho kappa_P); h (cell edge) is in the same length unit.
+ *   - Cell fields are [nz][ny][nx] row-major, x fastest.
+ *   - Boundary intensities Ib are [6][N]: one constant per domain face and
+ *     direction, faces ordered x-low, x-high, y-low, y-high, z-low, z-high.
+ *     NULL means vacuum (Ib = 0).
+ *   - Direction k is the k-th HEALPix ring-scheme pixel centre (ring by ring
+ *     from the north pole, increasing azimuth), rotated by the configured
+ *     quaternion.  vet_directions() returns the table.
+ *   - Moments are [10][cells]: E, Fx, Fy, Fz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz.
+ *   - The tensor f is [6][cells]: xx, yy, zz, xy, xz, yz.  Where E does not
+ *     exceed 1e-30 times the grid's largest E (no radiation arrives, or it
+ *     underflowed), f is the isotropic tensor I/3.
+ *   - Field pointers may be device memory or host memory (pageable or
+ *     pinned); the library detects which with cudaPointerGetAttributes and
+ *     stages host data through its own device buffers.  The caller owns all
+ *     field memory; the context owns its workspace.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous for device pointers.  Calls given host
+ *     pointers synchronise the stream before returning.
+ *   - Argument errors are returned at once and nothing is enqueued.  A
+ *     failure of an enqueued kernel is reported by the next call or by
+ *     vet_sync().  vet_last_error() gives a message for the last failure on
+ *     the context.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef VET_H
+#define VET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VET_OK = 0,
+  VET_EINVAL = 1,       /* bad argument (null pointer, size, precision) */
+  VET_ENOMEM = 2,       /* device or host allocation failed */
+  VET_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  VET_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+  VET_EUNSUPPORTED = 5  /* valid request this build cannot serve */
+} vet_status;
+
+#define VET_FP32 0 /* float fields, FP32 ray march and moments */
+#define VET_FP64 1 /* double fields, FP64 everywhere */
+
+/* Uniform grid of nx x ny x nz cells of edge h, cut into cubic blocks of
+ * `block` cells per edge; block must divide nx, ny and nz.  Hybrid
+ * characteristics run long characteristics inside each block
+ * (Sec. 2.2.5, via Buntemeyer et al. 2016). */
+typedef struct {
+  int nx, ny, nz;
+  int block; /* 2..32 */
+  double h;  /* > 0 */
+} vet_grid;
+
+/* Direction set and arithmetic.  nside is the HEALPix resolution (a power of
+ * two, 1..16; N = 12 nside^2).  rot_q is a quaternion (w, x, y, z) applied to
+ * every direction, the paper's random rotation of the HEALPix set
+ * (Sec. 2.2.5); it is normalised internally, (1,0,0,0) means no rotation. */
+typedef struct {
+  int nside;
+  double rot_q[4];
+  int precision; /* VET_FP32 or VET_FP64 */
+  int device;    /* CUDA device ordinal the context works on */
+} vet_config;
+
+typedef struct vet_ctx vet_ctx;
+
+/* Create a context: validates grid and config, builds the direction set and
+ * the per-direction ray templates, allocates the face-intensity workspace
+ * (N x blocks x 3 x (block+1)^2 values).  *out is NULL on failure. */
+vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_config *cfg);
+
+/* Release the context and all its device memory.  NULL is accepted. */
+vet_status vet_destroy(vet_ctx *ctx);
+
+/* Number of directions N, or -1 for a NULL context. */
+int vet_num_directions(const vet_ctx *ctx);
+
+/* Copy the direction table to host memory dirs_out[N][4] = (nx, ny, nz, w),
+ * FP64, in the documented HEALPix order. */
+vet_status vet_directions(const vet_ctx *ctx, double *dirs_out);
+
+/* Formal solution of Eq. 14 for all N directions (Sec. 2.2.5):
+ * I_out[N][cells] = cell-centre intensities.  FP32 context only. */
+vet_status vet_trace(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, float *I_out,
+                     void *stream);
+
+/* Angular quadratures of given intensities (Eqs. 6-8, c = 1):
+ * I[N][cells] -> M_out[10][cells].  FP32 context only. */
+vet_status vet_moments(vet_ctx *ctx, const float *I, float *M_out, void *stream);
+
+/* Whole closure, fused: trace + quadratures + f = P/E (Eq. 9) without
+ * storing I.  f_out[6][cells] required; M_out[10][cells] optional (NULL).
+ * FP32 context only. */
+vet_status vet_closure(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, float *f_out,
+                       float *M_out, void *stream);
+
+/* The same three operations on double fields, FP64 context only. */
+vet_status vet_trace_f64(vet_ctx *ctx, const double *kappa, const double *S, const double *Ib,
+                         double *I_out, void *stream);
+vet_status vet_moments_f64(vet_ctx *ctx, const double *I, double *M_out, void *stream);
+vet_status vet_closure_f64(vet_ctx *ctx, const double *kappa, const double *S, const double *Ib,
+                           double *f_out, double *M_out, void *stream);
+
+/* Wait for the context's last enqueued work and report any device error. */
+vet_status vet_sync(vet_ctx *ctx);
+
+/* Work measure of one closure, from the ray templates: the number of
+ * cell-ray segments and face-node-ray segments (one exponential each)
+ * summed over all cells, face nodes and directions. */
+vet_status vet_work_counts(const vet_ctx *ctx, long long *cell_segments, long long *face_segments);
+
+/* Message for the last failure on ctx (or for the last vet_create failure
+ * in this thread when ctx is NULL).  Never NULL. */
+const char *vet_last_error(const vet_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VET_H */

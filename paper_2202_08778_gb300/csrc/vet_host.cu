@@ -1,0 +1,651 @@
+// vet_host.cu -- host side of libvet: argument checks, the HEALPix direction
+// set, per-direction ray templates, the wavefront schedule of the face pass,
+// workspace, and the exported C ABI declared in include/vet.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "vet.h"
+#include "vet_internal.h"
+
+#define VET_API extern "C" __attribute__((visibility("default")))
+
+using vet::FaceItem;
+using vet::GridDims;
+
+struct vet_ctx {
+  vet_grid grid{};
+  vet_config cfg{};
+  GridDims dims{};
+  int N = 0;
+  int nblk = 0;
+  int nlevels = 0;
+  bool fp64 = false;
+  std::vector<double> dirs_ext;  // [N][4] in HEALPix order
+  std::vector<int> level_off;    // face items of level L: [level_off[L], level_off[L+1])
+  void *d_tpl = nullptr;         // N template blobs, internal (octant-sorted) order
+  FaceItem *d_items = nullptr;
+  void *d_faces = nullptr;       // [N][blocks][3][(B+1)^2]
+  void *d_emax = nullptr;        // 8 bytes: bit pattern of max E (nonnegative)
+  void *d_E = nullptr;           // [cells] E when the caller does not want M
+  void *d_coef = nullptr;        // [N][10] w (1, n, nn), HEALPix order
+  void *d_stage = nullptr;       // staging of host-pointer arguments
+  size_t stage_bytes = 0;
+  long long cell_segs = 0, face_segs = 0;
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+vet_status set_err(vet_ctx *c, vet_status st, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return st;
+}
+
+vet_status cuda_err(vet_ctx *c, cudaError_t e, const char *what) {
+  return set_err(c, e == cudaErrorMemoryAllocation ? VET_ENOMEM : VET_ECUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Switches to the context's device for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// HEALPix ring-scheme pixel centres (Gorski et al. 2005, Sec. 4): north cap
+// rings i < nside at z = 1 - i^2/(3 nside^2) with 4i pixels at
+// phi = (j - 1/2) pi/(2i); equatorial rings nside <= i <= 3 nside at
+// z = 4/3 - 2i/(3 nside) with 4 nside pixels at phi = (j - s/2) pi/(2 nside),
+// s = (i - nside + 1) mod 2; south cap mirrored.  Then rotated by the unit
+// quaternion q (the paper's random rotation, Sec. 2.2.5).
+void healpix_directions(int nside, const double q_in[4], std::vector<double> &out) {
+  const double pi = 3.14159265358979323846;
+  const int N = 12 * nside * nside;
+  double qn = std::sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+  const double qw = q_in[0] / qn, qx = q_in[1] / qn, qy = q_in[2] / qn, qz = q_in[3] / qn;
+  const double R[3][3] = {
+      {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+      {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+      {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+  out.assign((size_t)N * 4, 0.0);
+  int p = 0;
+  for (int ring = 1; ring < 4 * nside; ++ring) {
+    int cnt;
+    double z, first, step;
+    if (ring < nside || ring > 3 * nside) {
+      const int i = ring < nside ? ring : 4 * nside - ring;
+      const double zz = 1.0 - double(i) * i / (3.0 * nside * nside);
+      z = ring < nside ? zz : -zz;
+      cnt = 4 * i;
+      step = pi / (2.0 * i);
+      first = 0.5 * step;
+    } else {
+      z = 4.0 / 3.0 - 2.0 * ring / (3.0 * nside);
+      const int s = (ring - nside + 1) % 2;
+      cnt = 4 * nside;
+      step = pi / (2.0 * nside);
+      first = step * (1.0 - 0.5 * s);
+    }
+    const double sin_t = std::sqrt((1.0 - z) * (1.0 + z));
+    for (int j = 0; j < cnt; ++j, ++p) {
+      const double phi = first + j * step;
+      const double v[3] = {sin_t * std::cos(phi), sin_t * std::sin(phi), z};
+      for (int a = 0; a < 3; ++a) out[4 * p + a] = R[a][0] * v[0] + R[a][1] * v[1] + R[a][2] * v[2];
+      out[4 * p + 3] = 4.0 * pi / N;
+    }
+  }
+}
+
+struct Event {
+  double t;
+  int axis, m;
+};
+
+void merge_events(std::vector<Event> &ev) {
+  std::stable_sort(ev.begin(), ev.end(), [](const Event &a, const Event &b) {
+    return a.t < b.t || (a.t == b.t && a.axis < b.axis);
+  });
+}
+
+// Ray templates of one direction for block edge B (cell units; segment
+// lengths are stored as -length * h * log2(e)), written into the blob `out`
+// laid out by tpl_layout.  Returns the segments a block's cell rays and
+// face-node rays cross for this direction.
+template <typename R>
+void build_template(const double *d, int ext, int B, double h, unsigned char *out, long long &cell_segs,
+                    long long &node_segs) {
+  const vet::TplLayout L = vet::tpl_layout<R>(B);
+  std::memset(out, 0, L.bytes);
+  auto *hd = reinterpret_cast<vet::TplHead<R> *>(out);
+  R *clen = reinterpret_cast<R *>(out + L.clen);
+  R *nlen = reinterpret_cast<R *>(out + L.nlen);
+  int16_t *cdlt = reinterpret_cast<int16_t *>(out + L.cdlt);
+  int16_t *ndlt = reinterpret_cast<int16_t *>(out + L.ndlt);
+  int16_t *cpos = reinterpret_cast<int16_t *>(out + L.cpos);
+  int16_t *npos = reinterpret_cast<int16_t *>(out + L.npos);
+  int16_t *ck = reinterpret_cast<int16_t *>(out + L.ck);
+  R *cw = reinterpret_cast<R *>(out + L.cw);
+  int16_t *nk = reinterpret_cast<int16_t *>(out + L.nk);
+  R *nw = reinterpret_cast<R *>(out + L.nw);
+  const double scale = -h * 1.4426950408889634074;  // -h log2(e)
+  double an[3];
+  int sgn[3];
+  for (int a = 0; a < 3; ++a) {
+    hd->n[a] = R(d[a]);
+    an[a] = std::fabs(d[a]);
+    sgn[a] = d[a] < 0.0 ? -1 : 1;
+    hd->sgn[a] = sgn[a];
+  }
+  hd->w = R(d[3]);
+  hd->ext = ext;
+  const int stride[3] = {1, B, B * B};
+  // cell rays: planes at t = (m + 1/2)/|n_a|, m = 0..B-1
+  std::vector<Event> ev;
+  for (int a = 0; a < 3; ++a)
+    if (an[a] > 0.0)
+      for (int m = 0; m < B; ++m) ev.push_back({(m + 0.5) / an[a], a, m});
+  merge_events(ev);
+  for (int i = 0; i < 3 * B; ++i) cpos[i] = vet::kNever;
+  double prev = 0.0;
+  for (size_t e = 0; e < ev.size(); ++e) {
+    cpos[ev[e].axis * B + ev[e].m] = (int16_t)e;
+    clen[e] = R((ev[e].t - prev) * scale);
+    cdlt[e] = (int16_t)(-sgn[ev[e].axis] * stride[ev[e].axis]);
+    prev = ev[e].t;
+  }
+  // node rays: planes at t = m/|n_a|, m = 1..B
+  ev.clear();
+  for (int a = 0; a < 3; ++a)
+    if (an[a] > 0.0)
+      for (int m = 1; m <= B; ++m) ev.push_back({m / an[a], a, m});
+  merge_events(ev);
+  for (int a = 0; a < 3; ++a) {
+    npos[a * (B + 1)] = -1;
+    for (int m = 1; m <= B; ++m) npos[a * (B + 1) + m] = vet::kNever;
+  }
+  prev = 0.0;
+  for (size_t e = 0; e < ev.size(); ++e) {
+    npos[ev[e].axis * (B + 1) + ev[e].m] = (int16_t)e;
+    nlen[e] = R((ev[e].t - prev) * scale);
+    ndlt[e] = (int16_t)(-sgn[ev[e].axis] * stride[ev[e].axis]);
+    prev = ev[e].t;
+  }
+  // exit tables: leaving through axis a at depth D, the in-plane upwind-frame
+  // offset along axis b is d = off - (D / |n_a|) |n_b| (off = 1/2 for cells,
+  // 0 for nodes); stored as k = floor(d) and (f, 1 - f), f = d - k.
+  auto fill_exit = [&](int16_t *K, R *W, int rows, bool cells) {
+    for (int a = 0; a < 3; ++a) {
+      const int bc[2] = {a == 0 ? 1 : 0, a == 2 ? 1 : 2};
+      for (int j = 0; j < 2; ++j)
+        for (int l = 0; l < rows; ++l) {
+          const int idx = (a * 2 + j) * rows + l;
+          double dd = 0.0;
+          if (an[a] > 0.0) {
+            const double depth = cells ? l + 0.5 : (double)l;
+            const double t = depth / an[a];
+            dd = (cells ? 0.5 : 0.0) - t * an[bc[j]];
+          }
+          const double k = std::floor(dd);
+          const double f = dd - k;
+          K[idx] = (int16_t)k;
+          W[2 * idx] = R(f);
+          W[2 * idx + 1] = R(1.0 - f);
+        }
+    }
+  };
+  fill_exit(ck, cw, B, true);
+  fill_exit(nk, nw, B + 1, false);
+  // work measure: segments = exit event index + 1 per ray
+  long long cs = 0, ns = 0;
+  for (int l2 = 0; l2 < B; ++l2)
+    for (int l1 = 0; l1 < B; ++l1)
+      for (int l0 = 0; l0 < B; ++l0)
+        cs += 1 + std::min({(int)cpos[l0], (int)cpos[B + l1], (int)cpos[2 * B + l2]});
+  for (int a = 0; a < 3; ++a) {
+    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+    for (int u = 0; u <= B; ++u)
+      for (int v = 0; v <= B; ++v) {
+        int P[3];
+        P[a] = sgn[a] > 0 ? B : 0;
+        P[b] = u;
+        P[c] = v;
+        int Lq[3];
+        for (int q = 0; q < 3; ++q) Lq[q] = sgn[q] > 0 ? P[q] : B - P[q];
+        ns += 1 + std::min({(int)npos[Lq[0]], (int)npos[(B + 1) + Lq[1]], (int)npos[2 * (B + 1) + Lq[2]]});
+      }
+  }
+  cell_segs = cs;
+  node_segs = ns;
+}
+
+int octant_of(const double *d) { return (d[0] < 0) + 2 * (d[1] < 0) + 4 * (d[2] < 0); }
+
+void free_ctx(vet_ctx *c) {
+  if (!c) return;
+  cudaFree(c->d_tpl);
+  cudaFree(c->d_items);
+  cudaFree(c->d_faces);
+  cudaFree(c->d_emax);
+  cudaFree(c->d_E);
+  cudaFree(c->d_coef);
+  cudaFree(c->d_stage);
+  delete c;
+}
+
+template <typename R>
+vet_status build_context(vet_ctx *c) {
+  const int B = c->grid.block, N = c->N;
+  // internal order: octant-major, HEALPix order within an octant
+  std::vector<int> order(N);
+  for (int k = 0; k < N; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return octant_of(&c->dirs_ext[4 * a]) < octant_of(&c->dirs_ext[4 * b]);
+  });
+  const int tbytes = vet::tpl_layout<R>(B).bytes;
+  std::vector<unsigned char> tpl((size_t)tbytes * N);
+  long long cs_tot = 0, ns_tot = 0;
+  for (int i = 0; i < N; ++i) {
+    long long cs, ns;
+    build_template<R>(&c->dirs_ext[4 * order[i]], order[i], B, c->grid.h, tpl.data() + (size_t)i * tbytes, cs, ns);
+    cs_tot += cs;
+    ns_tot += ns;
+  }
+  c->cell_segs = cs_tot * c->nblk;
+  c->face_segs = ns_tot * c->nblk;
+  // face-pass schedule: level L of a block in octant o is its upwind-ordered
+  // index sum; one item = (block, up to kGroup directions of one octant).
+  const int kGroup = 4;
+  const int nb[3] = {c->dims.nbx, c->dims.nby, c->dims.nbz};
+  c->nlevels = nb[0] + nb[1] + nb[2] - 2;
+  std::vector<std::vector<FaceItem>> per_level(c->nlevels);
+  int ob[9] = {0};
+  for (int i = 0; i < N; ++i) ob[octant_of(&c->dirs_ext[4 * order[i]]) + 1]++;
+  for (int o = 0; o < 8; ++o) ob[o + 1] += ob[o];
+  for (int o = 0; o < 8; ++o) {
+    if (ob[o + 1] == ob[o]) continue;
+    const int s[3] = {(o & 1) ? -1 : 1, (o & 2) ? -1 : 1, (o & 4) ? -1 : 1};
+    for (int bz = 0; bz < nb[2]; ++bz)
+      for (int by = 0; by < nb[1]; ++by)
+        for (int bx = 0; bx < nb[0]; ++bx) {
+          const int bb[3] = {bx, by, bz};
+          int L = 0;
+          for (int a = 0; a < 3; ++a) L += s[a] > 0 ? bb[a] : nb[a] - 1 - bb[a];
+          const int id = (bz * nb[1] + by) * nb[0] + bx;
+          for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += kGroup)
+            per_level[L].push_back({id, d0, std::min(kGroup, ob[o + 1] - d0), 0});
+        }
+  }
+  std::vector<FaceItem> items;
+  c->level_off.assign(c->nlevels + 1, 0);
+  for (int L = 0; L < c->nlevels; ++L) {
+    c->level_off[L] = (int)items.size();
+    items.insert(items.end(), per_level[L].begin(), per_level[L].end());
+  }
+  c->level_off[c->nlevels] = (int)items.size();
+  // moment coefficients in HEALPix order
+  std::vector<R> coef((size_t)N * 10);
+  for (int k = 0; k < N; ++k) {
+    const double *d = &c->dirs_ext[4 * k];
+    const double w = d[3], x = d[0], y = d[1], z = d[2];
+    const double v[10] = {w, w * x, w * y, w * z, w * x * x, w * y * y, w * z * z, w * x * y, w * x * z, w * y * z};
+    for (int m = 0; m < 10; ++m) coef[(size_t)k * 10 + m] = R(v[m]);
+  }
+  cudaError_t e;
+  const size_t face_elems = (size_t)N * c->nblk * 3 * c->dims.nnode;
+  if ((e = cudaMalloc(&c->d_tpl, tpl.size()))) return cuda_err(c, e, "cudaMalloc(templates)");
+  if ((e = cudaMalloc((void **)&c->d_items, sizeof(FaceItem) * std::max<size_t>(1, items.size()))))
+    return cuda_err(c, e, "cudaMalloc(schedule)");
+  if ((e = cudaMalloc(&c->d_faces, sizeof(R) * face_elems))) return cuda_err(c, e, "cudaMalloc(face intensities)");
+  if ((e = cudaMalloc(&c->d_emax, 8))) return cuda_err(c, e, "cudaMalloc(emax)");
+  if ((e = cudaMalloc(&c->d_E, sizeof(R) * c->dims.ncell))) return cuda_err(c, e, "cudaMalloc(E)");
+  if ((e = cudaMalloc(&c->d_coef, sizeof(R) * coef.size()))) return cuda_err(c, e, "cudaMalloc(coef)");
+  if ((e = cudaMemcpy(c->d_tpl, tpl.data(), tpl.size(), cudaMemcpyHostToDevice)))
+    return cuda_err(c, e, "upload templates");
+  if (!items.empty() &&
+      (e = cudaMemcpy(c->d_items, items.data(), sizeof(FaceItem) * items.size(), cudaMemcpyHostToDevice)))
+    return cuda_err(c, e, "upload schedule");
+  if ((e = cudaMemcpy(c->d_coef, coef.data(), sizeof(R) * coef.size(), cudaMemcpyHostToDevice)))
+    return cuda_err(c, e, "upload coefficients");
+  if ((e = vet::prepare_kernels())) return cuda_err(c, e, "cudaFuncSetAttribute");
+  return VET_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device views of the caller's arguments; host arguments are staged.
+struct Staging {
+  vet_ctx *c;
+  size_t used = 0;
+  bool any_host = false;
+  std::vector<std::pair<void *, const void *>> d2h;  // (host dst, device src)
+  std::vector<size_t> d2h_bytes;
+};
+
+vet_status reserve_stage(vet_ctx *c, size_t bytes) {
+  if (bytes <= c->stage_bytes) return VET_OK;
+  cudaFree(c->d_stage);
+  c->d_stage = nullptr;
+  c->stage_bytes = 0;
+  cudaError_t e = cudaMalloc(&c->d_stage, bytes);
+  if (e) return cuda_err(c, e, "cudaMalloc(staging)");
+  c->stage_bytes = bytes;
+  return VET_OK;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename R>
+vet_status check_ctx(vet_ctx *c, bool want_fp64) {
+  if (!c) return VET_EINVAL;
+  if (c->fp64 != want_fp64)
+    return set_err(c, VET_EINVAL, want_fp64 ? "FP64 entry point on an FP32 context" : "FP32 entry point on an FP64 context");
+  return VET_OK;
+}
+
+// Prepares device pointers for a call.  ins: inputs (ptr, elements, may be
+// null); outs: outputs.  Host pointers are copied to / from the staging
+// buffer on `st`.
+template <typename R>
+vet_status stage_args(vet_ctx *c, cudaStream_t st, std::vector<std::pair<const R *, size_t>> ins,
+                      std::vector<std::pair<R *, size_t>> outs, std::vector<const R *> &din,
+                      std::vector<R *> &dout, std::vector<std::pair<R *, R *>> &copy_back,
+                      std::vector<size_t> &copy_bytes) {
+  size_t need = 0;
+  std::vector<bool> in_host(ins.size()), out_host(outs.size());
+  for (size_t i = 0; i < ins.size(); ++i) {
+    in_host[i] = ins[i].first && !is_device_ptr(ins[i].first);
+    if (in_host[i]) need += round256(ins[i].second * sizeof(R));
+  }
+  for (size_t i = 0; i < outs.size(); ++i) {
+    out_host[i] = outs[i].first && !is_device_ptr(outs[i].first);
+    if (out_host[i]) need += round256(outs[i].second * sizeof(R));
+  }
+  if (need) {
+    vet_status s = reserve_stage(c, need);
+    if (s != VET_OK) return s;
+  }
+  char *base = (char *)c->d_stage;
+  size_t off = 0;
+  din.clear();
+  dout.clear();
+  for (size_t i = 0; i < ins.size(); ++i) {
+    if (!in_host[i]) {
+      din.push_back(ins[i].first);
+      continue;
+    }
+    R *d = (R *)(base + off);
+    off += round256(ins[i].second * sizeof(R));
+    cudaError_t e = cudaMemcpyAsync(d, ins[i].first, ins[i].second * sizeof(R), cudaMemcpyHostToDevice, st);
+    if (e) return cuda_err(c, e, "host-to-device copy");
+    din.push_back(d);
+  }
+  for (size_t i = 0; i < outs.size(); ++i) {
+    if (!out_host[i]) {
+      dout.push_back(outs[i].first);
+      continue;
+    }
+    R *d = (R *)(base + off);
+    off += round256(outs[i].second * sizeof(R));
+    dout.push_back(d);
+    copy_back.push_back({outs[i].first, d});
+    copy_bytes.push_back(outs[i].second * sizeof(R));
+  }
+  return VET_OK;
+}
+
+template <typename R>
+vet_status finish_args(vet_ctx *c, cudaStream_t st, const std::vector<std::pair<R *, R *>> &copy_back,
+                       const std::vector<size_t> &bytes, bool had_host) {
+  for (size_t i = 0; i < copy_back.size(); ++i) {
+    cudaError_t e = cudaMemcpyAsync(copy_back[i].first, copy_back[i].second, bytes[i], cudaMemcpyDeviceToHost, st);
+    if (e) return cuda_err(c, e, "device-to-host copy");
+  }
+  if (had_host) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e) return cuda_err(c, e, "stream synchronize");
+  }
+  return VET_OK;
+}
+
+template <typename R>
+vet_status run_face_pass(vet_ctx *c, const R *kappa, const R *S, const R *Ib, cudaStream_t st) {
+  for (int L = 0; L < c->nlevels; ++L) {
+    const int n = c->level_off[L + 1] - c->level_off[L];
+    cudaError_t e = vet::launch_face_level<R>(c->dims, kappa, S, Ib, (const unsigned char *)c->d_tpl,
+                                               c->d_items + c->level_off[L], n, (R *)c->d_faces, st);
+    if (e) return cuda_err(c, e, "face pass launch");
+  }
+  return VET_OK;
+}
+
+template <typename R>
+vet_status do_trace(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *I_out, void *stream, bool fp64) {
+  vet_status s = check_ctx<R>(c, fp64);
+  if (s) return s;
+  if (!kappa || !S || !I_out) return set_err(c, VET_EINVAL, "kappa, S and I_out are required");
+  DeviceGuard dg(c->cfg.device);
+  if (!dg.ok) return set_err(c, VET_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nc = (size_t)c->dims.ncell;
+  std::vector<const R *> din;
+  std::vector<R *> dout;
+  std::vector<std::pair<R *, R *>> back;
+  std::vector<size_t> bytes;
+  s = stage_args<R>(c, st, {{kappa, nc}, {S, nc}, {Ib, Ib ? (size_t)6 * c->N : 0}}, {{I_out, (size_t)c->N * nc}},
+                    din, dout, back, bytes);
+  if (s) return s;
+  const bool had_host = !back.empty() || din[0] != kappa || din[1] != S || din[2] != Ib;
+  if ((s = run_face_pass<R>(c, din[0], din[1], din[2], st))) return s;
+  cudaError_t e = vet::launch_cell_pass<R>(c->dims, 1, din[0], din[1], din[2], (const unsigned char *)c->d_tpl,
+                                           (const R *)c->d_faces, dout[0], nullptr, nullptr, nullptr, nullptr, st);
+  if (e) return cuda_err(c, e, "cell pass launch");
+  c->last_stream = st;
+  return finish_args<R>(c, st, back, bytes, had_host);
+}
+
+template <typename R>
+vet_status do_moments(vet_ctx *c, const R *I, R *M_out, void *stream, bool fp64) {
+  vet_status s = check_ctx<R>(c, fp64);
+  if (s) return s;
+  if (!I || !M_out) return set_err(c, VET_EINVAL, "I and M_out are required");
+  DeviceGuard dg(c->cfg.device);
+  if (!dg.ok) return set_err(c, VET_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nc = (size_t)c->dims.ncell;
+  std::vector<const R *> din;
+  std::vector<R *> dout;
+  std::vector<std::pair<R *, R *>> back;
+  std::vector<size_t> bytes;
+  s = stage_args<R>(c, st, {{I, (size_t)c->N * nc}}, {{M_out, 10 * nc}}, din, dout, back, bytes);
+  if (s) return s;
+  const bool had_host = !back.empty() || din[0] != I;
+  cudaError_t e = vet::launch_moments<R>(c->dims.ncell, c->N, din[0], (const R *)c->d_coef, dout[0], st);
+  if (e) return cuda_err(c, e, "moments launch");
+  c->last_stream = st;
+  return finish_args<R>(c, st, back, bytes, had_host);
+}
+
+template <typename R>
+vet_status do_closure(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *f_out, R *M_out, void *stream,
+                      bool fp64) {
+  vet_status s = check_ctx<R>(c, fp64);
+  if (s) return s;
+  if (!kappa || !S || !f_out) return set_err(c, VET_EINVAL, "kappa, S and f_out are required");
+  DeviceGuard dg(c->cfg.device);
+  if (!dg.ok) return set_err(c, VET_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nc = (size_t)c->dims.ncell;
+  std::vector<const R *> din;
+  std::vector<R *> dout;
+  std::vector<std::pair<R *, R *>> back;
+  std::vector<size_t> bytes;
+  s = stage_args<R>(c, st, {{kappa, nc}, {S, nc}, {Ib, Ib ? (size_t)6 * c->N : 0}},
+                    {{f_out, 6 * nc}, {M_out, M_out ? 10 * nc : 0}}, din, dout, back, bytes);
+  if (s) return s;
+  const bool had_host = !back.empty() || din[0] != kappa || din[1] != S || din[2] != Ib;
+  cudaError_t e = cudaMemsetAsync(c->d_emax, 0, 8, st);
+  if (e) return cuda_err(c, e, "cudaMemsetAsync");
+  if ((s = run_face_pass<R>(c, din[0], din[1], din[2], st))) return s;
+  R *Mdev = dout[1];
+  e = vet::launch_cell_pass<R>(c->dims, 0, din[0], din[1], din[2], (const unsigned char *)c->d_tpl,
+                               (const R *)c->d_faces, nullptr, Mdev, (R *)c->d_E, dout[0], c->d_emax, st);
+  if (e) return cuda_err(c, e, "cell pass launch");
+  const R *E = Mdev ? Mdev : (const R *)c->d_E;
+  e = vet::launch_floor_fix<R>(c->dims.ncell, E, 1, c->d_emax, 1e-30, dout[0], st);
+  if (e) return cuda_err(c, e, "floor launch");
+  c->last_stream = st;
+  return finish_args<R>(c, st, back, bytes, had_host);
+}
+
+}  // namespace
+
+VET_API vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_config *cfg) {
+  if (!out) return set_err(nullptr, VET_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid || !cfg) return set_err(nullptr, VET_EINVAL, "grid and cfg are required");
+  const vet_grid g = *grid;
+  if (g.block < 2 || g.block > vet::kMaxBlock) return set_err(nullptr, VET_EINVAL, "block edge must be in 2..32");
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.nx % g.block || g.ny % g.block || g.nz % g.block)
+    return set_err(nullptr, VET_EINVAL, "grid extents must be positive multiples of the block edge");
+  if (!(g.h > 0.0) || !std::isfinite(g.h)) return set_err(nullptr, VET_EINVAL, "cell edge h must be positive");
+  if (cfg->nside < 1 || cfg->nside > 16 || (cfg->nside & (cfg->nside - 1)))
+    return set_err(nullptr, VET_EINVAL, "nside must be a power of two in 1..16");
+  if (cfg->precision != VET_FP32 && cfg->precision != VET_FP64)
+    return set_err(nullptr, VET_EINVAL, "precision must be VET_FP32 or VET_FP64");
+  const double qn = std::sqrt(cfg->rot_q[0] * cfg->rot_q[0] + cfg->rot_q[1] * cfg->rot_q[1] +
+                              cfg->rot_q[2] * cfg->rot_q[2] + cfg->rot_q[3] * cfg->rot_q[3]);
+  if (!(qn > 1e-12) || !std::isfinite(qn)) return set_err(nullptr, VET_EINVAL, "rotation quaternion is zero or not finite");
+  const bool fp64 = cfg->precision == VET_FP64;
+  const int nnode = (g.block + 1) * (g.block + 1);
+  if (vet::pass_smem_bytes(g.block, nnode, fp64) > 232448)
+    return set_err(nullptr, VET_EUNSUPPORTED, "block edge too large for one CTA's shared memory at this precision");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return set_err(nullptr, VET_ECUDA, "no CUDA device");
+  }
+  if (cfg->device < 0 || cfg->device >= ndev) return set_err(nullptr, VET_EINVAL, "device ordinal out of range");
+  vet_ctx *c = new (std::nothrow) vet_ctx;
+  if (!c) return set_err(nullptr, VET_ENOMEM, "host allocation failed");
+  c->grid = g;
+  c->cfg = *cfg;
+  c->fp64 = fp64;
+  c->N = 12 * cfg->nside * cfg->nside;
+  c->dims.nx = g.nx;
+  c->dims.ny = g.ny;
+  c->dims.nz = g.nz;
+  c->dims.B = g.block;
+  c->dims.nbx = g.nx / g.block;
+  c->dims.nby = g.ny / g.block;
+  c->dims.nbz = g.nz / g.block;
+  c->dims.nnode = nnode;
+  c->dims.ndir = c->N;
+  c->dims.ncell = (long long)g.nx * g.ny * g.nz;
+  c->nblk = c->dims.nbx * c->dims.nby * c->dims.nbz;
+  healpix_directions(cfg->nside, cfg->rot_q, c->dirs_ext);
+  vet_status s;
+  {
+    DeviceGuard dg(cfg->device);
+    if (!dg.ok) {
+      delete c;
+      return set_err(nullptr, VET_ECUDA, "cudaSetDevice failed");
+    }
+    s = fp64 ? build_context<double>(c) : build_context<float>(c);
+  }
+  if (s != VET_OK) {
+    g_create_err = c->err;
+    free_ctx(c);
+    return s;
+  }
+  *out = c;
+  return VET_OK;
+}
+
+VET_API vet_status vet_destroy(vet_ctx *ctx) {
+  if (!ctx) return VET_OK;
+  DeviceGuard dg(ctx->cfg.device);
+  free_ctx(ctx);
+  return VET_OK;
+}
+
+VET_API int vet_num_directions(const vet_ctx *ctx) { return ctx ? ctx->N : -1; }
+
+VET_API vet_status vet_directions(const vet_ctx *ctx, double *dirs_out) {
+  if (!ctx || !dirs_out) return VET_EINVAL;
+  std::memcpy(dirs_out, ctx->dirs_ext.data(), sizeof(double) * ctx->dirs_ext.size());
+  return VET_OK;
+}
+
+VET_API vet_status vet_trace(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, float *I_out,
+                             void *stream) {
+  return do_trace<float>(ctx, kappa, S, Ib, I_out, stream, false);
+}
+
+VET_API vet_status vet_moments(vet_ctx *ctx, const float *I, float *M_out, void *stream) {
+  return do_moments<float>(ctx, I, M_out, stream, false);
+}
+
+VET_API vet_status vet_closure(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, float *f_out,
+                               float *M_out, void *stream) {
+  return do_closure<float>(ctx, kappa, S, Ib, f_out, M_out, stream, false);
+}
+
+VET_API vet_status vet_trace_f64(vet_ctx *ctx, const double *kappa, const double *S, const double *Ib,
+                                 double *I_out, void *stream) {
+  return do_trace<double>(ctx, kappa, S, Ib, I_out, stream, true);
+}
+
+VET_API vet_status vet_moments_f64(vet_ctx *ctx, const double *I, double *M_out, void *stream) {
+  return do_moments<double>(ctx, I, M_out, stream, true);
+}
+
+VET_API vet_status vet_closure_f64(vet_ctx *ctx, const double *kappa, const double *S, const double *Ib,
+                                   double *f_out, double *M_out, void *stream) {
+  return do_closure<double>(ctx, kappa, S, Ib, f_out, M_out, stream, true);
+}
+
+VET_API vet_status vet_sync(vet_ctx *ctx) {
+  if (!ctx) return VET_EINVAL;
+  DeviceGuard dg(ctx->cfg.device);
+  cudaError_t e = cudaStreamSynchronize(ctx->last_stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e) return cuda_err(ctx, e, "device work failed");
+  return VET_OK;
+}
+
+VET_API vet_status vet_work_counts(const vet_ctx *ctx, long long *cell_segments, long long *face_segments) {
+  if (!ctx || !cell_segments || !face_segments) return VET_EINVAL;
+  *cell_segments = ctx->cell_segs;
+  *face_segments = ctx->face_segs;
+  return VET_OK;
+}
+
+VET_API const char *vet_last_error(const vet_ctx *ctx) {
+  if (!ctx) return g_create_err.c_str();
+  return ctx->err.c_str();
+}

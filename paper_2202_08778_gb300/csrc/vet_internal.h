@@ -1,0 +1,125 @@
+// vet_internal.h -- data shared by the host side and the kernels of libvet.
+//
+// Geometry is in cell units inside one block: memory-frame coordinates run
+// from 0 to B along each axis of the block; the "upwind frame" of a direction
+// flips every axis whose direction component is negative, so that backward
+// rays always move towards lower upwind-frame coordinates and a block's
+// upwind faces sit at upwind-frame coordinate 0.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace vet {
+
+constexpr int kMaxBlock = 32;             // largest block edge B
+constexpr int kNever = 0x3fff;            // event index of an axis the ray never exits by
+
+// Per-direction ray templates (Sec. 2.2.5 reading: long characteristics in a
+// block).  A backward ray from a cell centre crosses the block's cell planes
+// at parameters t = (m + 1/2)/|n_a| (m = 0, 1, ...) on axis a, independently
+// of which cell it starts from; merging the three sequences gives one event
+// list per direction.  A ray from a cell whose upwind-frame coordinate along
+// axis a is l_a leaves the block at the event (a, m = l_a), whichever of the
+// three comes first in the merged order (ties: lowest axis).  Face-node rays
+// start on lattice points and cross planes at t = m/|n_a| (m = 1, 2, ...).
+//
+// The exit point of a ray leaving through axis a after depth l (cells:
+// l + 1/2, nodes: l) has, along another axis b, the upwind-frame coordinate
+// l_b + d with d = (1/2 or 0) - depth |n_b|/|n_a|; d depends on the direction
+// and l only.  The host evaluates it in FP64 and stores k = floor(d) and the
+// interpolation weights (f, 1 - f), f = d - k, so that the device never forms
+// a position by cancellation.
+//
+// One direction's template is a byte blob laid out by TplLayout for the
+// block edge B: a TplHead followed by the arrays below (16-byte aligned).
+template <typename R>
+struct TplHead {
+  R n[3];     // direction
+  R w;        // quadrature weight 4 pi / N
+  int sgn[3]; // +1 if n_a >= 0 (a zero component counts as positive) else -1
+  int ext;    // index of this direction in the documented HEALPix order
+};
+
+struct TplLayout {
+  int clen;   // R[3B]        cell-ray segment e length, times h log2(e)
+  int nlen;   // R[3B]        node-ray segment lengths, times h log2(e)
+  int cdlt;   // int16[3B]    tile-index step at cell event e
+  int ndlt;   // int16[3B]    tile-index step at node event e
+  int cpos;   // int16[3][B]  merged index of cell event (a, m)
+  int npos;   // int16[3][B+1] merged index of node event (a, m); [a][0] = -1
+  int ck;     // int16[3][2][B]   floor(d) of cell exits
+  int cw;     // R[3][2][B][2]    (f, 1-f) of cell exits
+  int nk;     // int16[3][2][B+1] floor(d) of node exits
+  int nw;     // R[3][2][B+1][2]  (f, 1-f) of node exits
+  int bytes;  // total, a multiple of 16
+};
+
+__host__ __device__ inline int tpl_align16(int x) { return (x + 15) & ~15; }
+
+template <typename R>
+__host__ __device__ inline TplLayout tpl_layout(int B) {
+  TplLayout L;
+  int o = tpl_align16((int)sizeof(TplHead<R>));
+  L.clen = o; o = tpl_align16(o + 3 * B * (int)sizeof(R));
+  L.nlen = o; o = tpl_align16(o + 3 * B * (int)sizeof(R));
+  L.cdlt = o; o = tpl_align16(o + 3 * B * 2);
+  L.ndlt = o; o = tpl_align16(o + 3 * B * 2);
+  L.cpos = o; o = tpl_align16(o + 3 * B * 2);
+  L.npos = o; o = tpl_align16(o + 3 * (B + 1) * 2);
+  L.ck = o;   o = tpl_align16(o + 6 * B * 2);
+  L.cw = o;   o = tpl_align16(o + 6 * B * 2 * (int)sizeof(R));
+  L.nk = o;   o = tpl_align16(o + 6 * (B + 1) * 2);
+  L.nw = o;   o = tpl_align16(o + 6 * (B + 1) * 2 * (int)sizeof(R));
+  L.bytes = o;
+  return L;
+}
+
+// Fixed sizes of one launch.
+struct GridDims {
+  int nx, ny, nz;     // cells
+  int B;              // block edge
+  int nbx, nby, nbz;  // blocks
+  int nnode;          // (B+1)^2 face nodes per face
+  int ndir;           // directions
+  long long ncell;    // nx*ny*nz
+};
+
+// One work item of the face pass: a block and a run of directions of one
+// octant, all at the same wavefront level.
+struct FaceItem {
+  int block;
+  int dir_begin;  // internal direction index
+  int dir_count;
+  int pad_;
+};
+
+// Launchers (vet_kernels.cu).  All return the cudaGetLastError() of the
+// launch.  R = float or double.
+template <typename R>
+cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, const R *Ib,
+                              const unsigned char *tpl, const FaceItem *items, int nitems, R *faces,
+                              cudaStream_t st);
+
+// mode 0: moments + f (+ E for the floor rule); mode 1: write I_out.
+template <typename R>
+cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const R *Ib,
+                             const unsigned char *tpl, const R *faces, R *I_out, R *M_out, R *E_out,
+                             R *f_out, void *emax_bits, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_floor_fix(long long ncell, const R *E, long long E_stride, const void *emax_bits,
+                             double floor_rel, R *f_out, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef, R *M_out,
+                           cudaStream_t st);
+
+// Dynamic shared memory of one face-pass or cell-pass CTA.
+size_t pass_smem_bytes(int B, int nnode, bool fp64);
+
+// Per-device kernel attributes; call with the context's device current.
+cudaError_t prepare_kernels();
+
+}  // namespace vet

@@ -68,7 +68,7 @@ def gaussian_random_field(shape, rng, kmin=2.0, kmax=32.0, slope=-2.0) -> np.nda
     amp = np.zeros_like(k)
     band = (k >= kmin) & (k <= kmax)
     amp[band] = k[band] ** (0.5 * slope)
-    g = np.fft.irfftn(wk * amp, s=shape)
+    g = np.fft.irfftn(wk * amp, s=shape, axes=(0, 1, 2))
     g -= g.mean()
     sd = g.std()
     return g / sd if sd > 0 else g
