@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Throughput of the VET closure (VETTAM Sec. 2.2.5) on GB300.
+
+One step = one full closure (face wavefront pass, cell pass with the
+quadratures, f = P/E) over the 128^3 lognormal-opacity workload in 16^3
+blocks with 192 HEALPix directions (nside = 4), inputs resident in HBM.
+The metric is cell-angle updates per second (cells x directions / time) and
+closures per second, at the accuracy the parity tests hold (|df| <= 1e-6
+against the FP64 oracle).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line on rank 0.  With --gpus N > 1 (under torchrun) every
+rank runs an independent replica of the workload on its own GPU (the method
+has no data exchange between replicas); the value is the total over ranks
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G cell·angle updates/s and VET closures/s at fixed |Δf|≤1e-6 (plain) / ≤1e-2 (learned)"
+UNIT = "G cell·angle updates/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+MUFU_PER_CLK_PER_SM = 16    # ex2 results per clock per SM
+N_SM = 152
+
+
+def workload():
+    from paper_2202_08778_gb300 import synth
+
+    p = synth.lognormal_problem(n=128, B=16, nside=4, seed=2)
+    return p, {"workload": "lognormal128_B16_nside4", "grid": [128, 128, 128], "block": 16, "n_dir": 192,
+               "seed": 2, "boundary": "vacuum", "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(p, dirs, ndir_sample: int):
+    """Time the FP64 oracle (trace -> moments -> closure) on the workload's
+    grid restricted to an evenly spaced subset of directions.  Returns
+    (cell-angle updates per second, seconds, threads used, sample text)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    idx = np.linspace(0, dirs.shape[0] - 1, ndir_sample).round().astype(int)
+    sub = dirs[idx].copy()
+    cores = len(os.sched_getaffinity(0))
+    k = p["kappa"].astype(np.float32).astype(np.float64)
+    s = p["S"].astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    I = oracle.trace(k, s, sub, p["B"], p["h"], None, nthreads=cores)
+    M = oracle.moments(I, sub)
+    oracle.closure(M)
+    dt = time.perf_counter() - t0
+    upd = k.size * ndir_sample
+    return upd / dt, dt, min(cores, ndir_sample), (
+        f"{ndir_sample} of {dirs.shape[0]} directions (evenly spaced) over the full 128^3 grid, "
+        f"trace+moments+closure in FP64")
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm (host cores, rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+
+    p, cfg = workload()
+    oracle.build()
+    dirs = oracle.healpix(p["nside"], p["q"])
+    cores = len(os.sched_getaffinity(0))
+    nsub = min(dirs.shape[0], max(4, cores))
+    for _ in range(args.warmup):
+        oracle_sample(p, dirs, nsub)
+    ts = []
+    for _ in range(args.steps):
+        v, dt, used, sample = oracle_sample(p, dirs, nsub)
+        ts.append(dt)
+    upd = p["kappa"].size * nsub
+    value = upd * len(ts) / sum(ts) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2202_08778_gb300 import vet
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    p, cfg = workload()
+    n = p["kappa"].size
+    ctx = vet.Context(p["kappa"].shape, p["B"], p["h"], p["nside"], p["q"], device=local_rank)
+    N = ctx.N
+    k_h = np.ascontiguousarray(p["kappa"].astype(np.float32))
+    s_h = np.ascontiguousarray(p["S"].astype(np.float32))
+    kappa = torch.from_numpy(k_h).to(dev)
+    S = torch.from_numpy(s_h).to(dev)
+    f = torch.empty(6 * n, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    cell_segs, face_segs = ctx.work_counts()
+    launches = ctx.launches_per_closure()
+
+    for _ in range(args.warmup):
+        ctx.closure(kappa, S, None, f)
+    ctx.set_timing(True)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phase = []
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            ctx.closure(kappa, S, None, f)
+            ev[i][1].record(stream)
+            phase.append(ctx.last_timing())
+        torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ctx.set_timing(False)
+    ms_step = total_ms / args.steps
+    updates = float(n) * N * args.steps * world
+    value = updates / (total_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    kp = torch.from_numpy(k_h).pin_memory()
+    sp = torch.from_numpy(s_h).pin_memory()
+    fp = torch.empty(6 * n, dtype=torch.float32).pin_memory()
+    ctx.closure(kp, sp, None, fp)
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.closure(kp, sp, None, fp)  # stages H2D, computes, D2H, synchronises
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": float(n) * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
+           "d2h_bytes_per_step": 6 * n * 4, "ms_per_step": 1e3 * e2e_s}
+
+    # roofline of the dominant kernel (the cell pass), from the live events
+    cell_ms = statistics.median(ph[1] for ph in phase)
+    face_ms = statistics.median(ph[0] for ph in phase)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = MUFU_PER_CLK_PER_SM * N_SM * sm_max * 1e6 / 1e9  # G exp/s
+    achieved = cell_segs / (cell_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "cell_pass_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G exp/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "cell_pass_kernel<float,0>",
+                "peak_basis": f"MUFU ex2: {MUFU_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {sm_max:.0f} MHz",
+                "algorithmic": f"{cell_segs} cell-ray segments (one exp each) per launch"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "closures_per_s": 1e3 / ms_step * world,
+            "phases_ms": {"face_pass": face_ms, "cell_pass": cell_ms,
+                          "closing": statistics.median(ph[2] for ph in phase)},
+            "work": {"cell_segments": cell_segs, "face_segments": face_segs,
+                     "segments_per_cell_angle": (cell_segs + face_segs) / (n * N)},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps}
+    clocks = clk.summary()
+    if clocks is not None:
+        line["clocks"] = clocks
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = len(os.sched_getaffinity(0))
+        nsub = min(N, 2 * cores)
+        v, dt, used, sample = oracle_sample(p, ctx.directions(), nsub)
+        line["cpu_baseline"] = {"value": v / 1e9, "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": sample, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

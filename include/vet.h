@@ -133,6 +133,20 @@ vet_status vet_sync(vet_ctx *ctx);
  * summed over all cells, face nodes and directions. */
 vet_status vet_work_counts(const vet_ctx *ctx, long long *cell_segments, long long *face_segments);
 
+/* Per-phase device timing.  After vet_set_timing(ctx, 1), every vet_trace /
+ * vet_closure call records CUDA events on its stream around its phases;
+ * vet_last_timing() waits for the last call's events and writes, in
+ * milliseconds: ms[0] the face pass (all wavefront levels), ms[1] the cell
+ * pass (rays, quadratures and f), ms[2] the closing step (floor rule), ms[3]
+ * the whole call.  Timing is off by default. */
+vet_status vet_set_timing(vet_ctx *ctx, int enable);
+vet_status vet_last_timing(vet_ctx *ctx, float ms[4]);
+
+/* Kernel launches one vet_closure call makes (its work is split into this
+ * many kernels: one per wavefront level of the face pass, the cell pass and
+ * the closing step). */
+int vet_launches_per_closure(const vet_ctx *ctx);
+
 /* Message for the last failure on ctx (or for the last vet_create failure
  * in this thread when ctx is NULL).  Never NULL. */
 const char *vet_last_error(const vet_ctx *ctx);

@@ -38,6 +38,9 @@ struct vet_ctx {
   size_t stage_bytes = 0;
   long long cell_segs = 0, face_segs = 0;
   cudaStream_t last_stream = nullptr;
+  bool timing = false;
+  bool timed = false;            // events of the last call were recorded
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::string err;
 };
 
@@ -240,6 +243,8 @@ int octant_of(const double *d) { return (d[0] < 0) + 2 * (d[1] < 0) + 4 * (d[2] 
 
 void free_ctx(vet_ctx *c) {
   if (!c) return;
+  for (auto &e : c->ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(c->d_tpl);
   cudaFree(c->d_items);
   cudaFree(c->d_faces);
@@ -432,6 +437,15 @@ vet_status finish_args(vet_ctx *c, cudaStream_t st, const std::vector<std::pair<
   return VET_OK;
 }
 
+// Records timing event i on st when timing is enabled.
+vet_status mark(vet_ctx *c, int i, cudaStream_t st) {
+  if (!c->timing) return VET_OK;
+  cudaError_t e = cudaEventRecord(c->ev[i], st);
+  if (e) return cuda_err(c, e, "cudaEventRecord");
+  if (i == 3) c->timed = true;
+  return VET_OK;
+}
+
 template <typename R>
 vet_status run_face_pass(vet_ctx *c, const R *kappa, const R *S, const R *Ib, cudaStream_t st) {
   for (int L = 0; L < c->nlevels; ++L) {
@@ -460,10 +474,14 @@ vet_status do_trace(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *I_ou
                     din, dout, back, bytes);
   if (s) return s;
   const bool had_host = !back.empty() || din[0] != kappa || din[1] != S || din[2] != Ib;
+  c->timed = false;
+  if ((s = mark(c, 0, st))) return s;
   if ((s = run_face_pass<R>(c, din[0], din[1], din[2], st))) return s;
+  if ((s = mark(c, 1, st))) return s;
   cudaError_t e = vet::launch_cell_pass<R>(c->dims, 1, din[0], din[1], din[2], (const unsigned char *)c->d_tpl,
                                            (const R *)c->d_faces, dout[0], nullptr, nullptr, nullptr, nullptr, st);
   if (e) return cuda_err(c, e, "cell pass launch");
+  if ((s = mark(c, 2, st)) || (s = mark(c, 3, st))) return s;
   c->last_stream = st;
   return finish_args<R>(c, st, back, bytes, had_host);
 }
@@ -508,16 +526,21 @@ vet_status do_closure(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *f_
                     {{f_out, 6 * nc}, {M_out, M_out ? 10 * nc : 0}}, din, dout, back, bytes);
   if (s) return s;
   const bool had_host = !back.empty() || din[0] != kappa || din[1] != S || din[2] != Ib;
+  c->timed = false;
+  if ((s = mark(c, 0, st))) return s;
   cudaError_t e = cudaMemsetAsync(c->d_emax, 0, 8, st);
   if (e) return cuda_err(c, e, "cudaMemsetAsync");
   if ((s = run_face_pass<R>(c, din[0], din[1], din[2], st))) return s;
+  if ((s = mark(c, 1, st))) return s;
   R *Mdev = dout[1];
   e = vet::launch_cell_pass<R>(c->dims, 0, din[0], din[1], din[2], (const unsigned char *)c->d_tpl,
                                (const R *)c->d_faces, nullptr, Mdev, (R *)c->d_E, dout[0], c->d_emax, st);
   if (e) return cuda_err(c, e, "cell pass launch");
+  if ((s = mark(c, 2, st))) return s;
   const R *E = Mdev ? Mdev : (const R *)c->d_E;
   e = vet::launch_floor_fix<R>(c->dims.ncell, E, 1, c->d_emax, 1e-30, dout[0], st);
   if (e) return cuda_err(c, e, "floor launch");
+  if ((s = mark(c, 3, st))) return s;
   c->last_stream = st;
   return finish_args<R>(c, st, back, bytes, had_host);
 }
@@ -643,6 +666,41 @@ VET_API vet_status vet_work_counts(const vet_ctx *ctx, long long *cell_segments,
   *cell_segments = ctx->cell_segs;
   *face_segments = ctx->face_segs;
   return VET_OK;
+}
+
+VET_API vet_status vet_set_timing(vet_ctx *ctx, int enable) {
+  if (!ctx) return VET_EINVAL;
+  DeviceGuard dg(ctx->cfg.device);
+  if (enable && !ctx->ev[0]) {
+    for (auto &e : ctx->ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r) return cuda_err(ctx, r, "cudaEventCreate");
+    }
+  }
+  ctx->timing = enable != 0;
+  ctx->timed = false;
+  return VET_OK;
+}
+
+VET_API vet_status vet_last_timing(vet_ctx *ctx, float ms[4]) {
+  if (!ctx || !ms) return VET_EINVAL;
+  if (!ctx->timed) return set_err(ctx, VET_EINVAL, "no timed call since timing was enabled");
+  DeviceGuard dg(ctx->cfg.device);
+  cudaError_t e = cudaEventSynchronize(ctx->ev[3]);
+  if (e) return cuda_err(ctx, e, "cudaEventSynchronize");
+  const int from[4] = {0, 1, 2, 0}, to[4] = {1, 2, 3, 3};
+  for (int i = 0; i < 4; ++i) {
+    e = cudaEventElapsedTime(&ms[i], ctx->ev[from[i]], ctx->ev[to[i]]);
+    if (e) return cuda_err(ctx, e, "cudaEventElapsedTime");
+  }
+  return VET_OK;
+}
+
+VET_API int vet_launches_per_closure(const vet_ctx *ctx) {
+  if (!ctx) return -1;
+  int n = 0;
+  for (int L = 0; L < ctx->nlevels; ++L) n += ctx->level_off[L + 1] > ctx->level_off[L];
+  return n + 2;
 }
 
 VET_API const char *vet_last_error(const vet_ctx *ctx) {

@@ -27,7 +27,7 @@ _STATUS = {1: "VET_EINVAL", 2: "VET_ENOMEM", 3: "VET_ECUDA", 4: "VET_ETIMEOUT", 
 EXPORTS = (
     "vet_create", "vet_destroy", "vet_num_directions", "vet_directions", "vet_trace", "vet_moments",
     "vet_closure", "vet_trace_f64", "vet_moments_f64", "vet_closure_f64", "vet_sync", "vet_work_counts",
-    "vet_last_error",
+    "vet_set_timing", "vet_last_timing", "vet_launches_per_closure", "vet_last_error",
 )
 
 
@@ -81,10 +81,14 @@ def load(build_if_missing: bool = True):
             getattr(lib, name).argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.vet_sync.argtypes = [vp]
         lib.vet_work_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+        lib.vet_set_timing.argtypes = [vp, i]
+        lib.vet_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        lib.vet_launches_per_closure.argtypes = [vp]
+        lib.vet_launches_per_closure.restype = i
         lib.vet_last_error.argtypes = [vp]
         lib.vet_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("vet_num_directions", "vet_last_error"):
+            if name not in ("vet_num_directions", "vet_last_error", "vet_launches_per_closure"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -199,6 +203,18 @@ class Context:
                                             _ptr(Ib, dt, 6 * self.N, "Ib"), _ptr(f_out, dt, 6 * nc, "f_out"),
                                             _ptr(M_out, dt, 10 * nc, "M_out"), _stream(stream)))
         return f_out
+
+    def set_timing(self, enable: bool = True):
+        self._check(self._lib.vet_set_timing(self._h, int(bool(enable))))
+
+    def last_timing(self):
+        """(face pass, cell pass, closing step, whole call) in ms of the last call."""
+        ms = (ctypes.c_float * 4)()
+        self._check(self._lib.vet_last_timing(self._h, ms))
+        return tuple(float(v) for v in ms)
+
+    def launches_per_closure(self) -> int:
+        return int(self._lib.vet_launches_per_closure(self._h))
 
     def sync(self):
         self._check(self._lib.vet_sync(self._h))
