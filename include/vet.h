@@ -90,7 +90,7 @@ typedef struct vet_ctx vet_ctx;
 
 /* Create a context: validates grid and config, builds the direction set and
  * the per-direction ray templates, allocates the face-intensity workspace
- * (N x blocks x 3 x (block+1)^2 values).  *out is NULL on failure. */
+ * (N x blocks x 3 x about (block+2)^2 values).  *out is NULL on failure. */
 vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_config *cfg);
 
 /* Release the context and all its device memory.  NULL is accepted. */

@@ -30,7 +30,7 @@ struct vet_ctx {
   std::vector<int> level_off;    // face items of level L: [level_off[L], level_off[L+1])
   void *d_tpl = nullptr;         // N template blobs, internal (octant-sorted) order
   FaceItem *d_items = nullptr;
-  void *d_faces = nullptr;       // [N][blocks][3][(B+1)^2]
+  void *d_faces = nullptr;       // [N][blocks][3][fstride], upwind frame, padded
   void *d_emax = nullptr;        // 8 bytes: bit pattern of max E (nonnegative)
   void *d_E = nullptr;           // [cells] E when the caller does not want M
   void *d_coef = nullptr;        // [N][10] w (1, n, nn), HEALPix order
@@ -138,10 +138,8 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   const vet::TplLayout L = vet::tpl_layout<R>(B);
   std::memset(out, 0, L.bytes);
   auto *hd = reinterpret_cast<vet::TplHead<R> *>(out);
-  R *clen = reinterpret_cast<R *>(out + L.clen);
-  R *nlen = reinterpret_cast<R *>(out + L.nlen);
-  int16_t *cdlt = reinterpret_cast<int16_t *>(out + L.cdlt);
-  int16_t *ndlt = reinterpret_cast<int16_t *>(out + L.ndlt);
+  auto *cev = reinterpret_cast<vet::TplEvent<R> *>(out + L.cev);
+  auto *nev = reinterpret_cast<vet::TplEvent<R> *>(out + L.nev);
   int16_t *cpos = reinterpret_cast<int16_t *>(out + L.cpos);
   int16_t *npos = reinterpret_cast<int16_t *>(out + L.npos);
   int16_t *ck = reinterpret_cast<int16_t *>(out + L.ck);
@@ -170,8 +168,8 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   double prev = 0.0;
   for (size_t e = 0; e < ev.size(); ++e) {
     cpos[ev[e].axis * B + ev[e].m] = (int16_t)e;
-    clen[e] = R((ev[e].t - prev) * scale);
-    cdlt[e] = (int16_t)(-sgn[ev[e].axis] * stride[ev[e].axis]);
+    cev[e].len = R((ev[e].t - prev) * scale);
+    cev[e].delta = -sgn[ev[e].axis] * stride[ev[e].axis];
     prev = ev[e].t;
   }
   // node rays: planes at t = m/|n_a|, m = 1..B
@@ -187,8 +185,8 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   prev = 0.0;
   for (size_t e = 0; e < ev.size(); ++e) {
     npos[ev[e].axis * (B + 1) + ev[e].m] = (int16_t)e;
-    nlen[e] = R((ev[e].t - prev) * scale);
-    ndlt[e] = (int16_t)(-sgn[ev[e].axis] * stride[ev[e].axis]);
+    nev[e].len = R((ev[e].t - prev) * scale);
+    nev[e].delta = -sgn[ev[e].axis] * stride[ev[e].axis];
     prev = ev[e].t;
   }
   // exit tables: leaving through axis a at depth D, the in-plane upwind-frame
@@ -205,6 +203,11 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
             const double depth = cells ? l + 0.5 : (double)l;
             const double t = depth / an[a];
             dd = (cells ? 0.5 : 0.0) - t * an[bc[j]];
+            // an exit exactly on a face edge (a tie with axis b) may come out
+            // a rounding error below the integer; snap it so that the device
+            // never sees a node index below 0
+            const double r = std::nearbyint(dd);
+            if (std::fabs(dd - r) < 1e-12) dd = r;
           }
           const double k = std::floor(dd);
           const double f = dd - k;
@@ -314,11 +317,14 @@ vet_status build_context(vet_ctx *c) {
     for (int m = 0; m < 10; ++m) coef[(size_t)k * 10 + m] = R(v[m]);
   }
   cudaError_t e;
-  const size_t face_elems = (size_t)N * c->nblk * 3 * c->dims.nnode;
+  c->dims.fstride = vet::face_stride_elems<R>(B);
+  const size_t face_elems = (size_t)N * c->nblk * 3 * c->dims.fstride;
   if ((e = cudaMalloc(&c->d_tpl, tpl.size()))) return cuda_err(c, e, "cudaMalloc(templates)");
   if ((e = cudaMalloc((void **)&c->d_items, sizeof(FaceItem) * std::max<size_t>(1, items.size()))))
     return cuda_err(c, e, "cudaMalloc(schedule)");
   if ((e = cudaMalloc(&c->d_faces, sizeof(R) * face_elems))) return cuda_err(c, e, "cudaMalloc(face intensities)");
+  // the padding row and column of every stored face stay zero for good
+  if ((e = cudaMemset(c->d_faces, 0, sizeof(R) * face_elems))) return cuda_err(c, e, "cudaMemset(face intensities)");
   if ((e = cudaMalloc(&c->d_emax, 8))) return cuda_err(c, e, "cudaMalloc(emax)");
   if ((e = cudaMalloc(&c->d_E, sizeof(R) * c->dims.ncell))) return cuda_err(c, e, "cudaMalloc(E)");
   if ((e = cudaMalloc(&c->d_coef, sizeof(R) * coef.size()))) return cuda_err(c, e, "cudaMalloc(coef)");

@@ -42,11 +42,17 @@ struct TplHead {
   int ext;    // index of this direction in the documented HEALPix order
 };
 
+// One event of a ray template: the length of the segment that ends at it,
+// scaled by -h log2(e), and the tile-index step taken there.
+template <typename R>
+struct alignas(2 * sizeof(R)) TplEvent {
+  R len;
+  int delta;
+};
+
 struct TplLayout {
-  int clen;   // R[3B]        cell-ray segment e length, times h log2(e)
-  int nlen;   // R[3B]        node-ray segment lengths, times h log2(e)
-  int cdlt;   // int16[3B]    tile-index step at cell event e
-  int ndlt;   // int16[3B]    tile-index step at node event e
+  int cev;    // TplEvent<R>[3B]  cell-ray events
+  int nev;    // TplEvent<R>[3B]  node-ray events
   int cpos;   // int16[3][B]  merged index of cell event (a, m)
   int npos;   // int16[3][B+1] merged index of node event (a, m); [a][0] = -1
   int ck;     // int16[3][2][B]   floor(d) of cell exits
@@ -62,10 +68,8 @@ template <typename R>
 __host__ __device__ inline TplLayout tpl_layout(int B) {
   TplLayout L;
   int o = tpl_align16((int)sizeof(TplHead<R>));
-  L.clen = o; o = tpl_align16(o + 3 * B * (int)sizeof(R));
-  L.nlen = o; o = tpl_align16(o + 3 * B * (int)sizeof(R));
-  L.cdlt = o; o = tpl_align16(o + 3 * B * 2);
-  L.ndlt = o; o = tpl_align16(o + 3 * B * 2);
+  L.cev = o;  o = tpl_align16(o + 3 * B * (int)sizeof(TplEvent<R>));
+  L.nev = o;  o = tpl_align16(o + 3 * B * (int)sizeof(TplEvent<R>));
   L.cpos = o; o = tpl_align16(o + 3 * B * 2);
   L.npos = o; o = tpl_align16(o + 3 * (B + 1) * 2);
   L.ck = o;   o = tpl_align16(o + 6 * B * 2);
@@ -82,9 +86,19 @@ struct GridDims {
   int B;              // block edge
   int nbx, nby, nbz;  // blocks
   int nnode;          // (B+1)^2 face nodes per face
+  int fstride;        // elements per stored face: (B+2)^2 rounded up to 16 bytes
   int ndir;           // directions
   long long ncell;    // nx*ny*nz
 };
+
+// Stored faces: node (ub, uc) of a face, in the upwind frame of the direction
+// (the in-plane axes flipped where the direction component is negative), at
+// ub * (B + 2) + uc; row and column B + 1 are zero padding.
+template <typename R>
+__host__ __device__ inline int face_stride_elems(int B) {
+  const int per = 16 / (int)sizeof(R);
+  return ((B + 2) * (B + 2) + per - 1) / per * per;
+}
 
 // One work item of the face pass: a block and a run of directions of one
 // octant, all at the same wavefront level.

@@ -11,8 +11,11 @@
 //                 direction, with the quadratures E, F, P (Eqs. 6-8)
 //                 accumulated in registers across all directions and
 //                 f = P/E (Eq. 9) in the epilogue, so that I is never stored.
-// Both passes stage the block's kappa/S tile, the direction's ray template and
-// the three incoming faces in shared memory.
+// Both passes stage the block's kappa/S tile, the directions' ray templates
+// and the incoming faces in shared memory.  Faces are stored by the face pass
+// already in the consumer's upwind frame and padded, so staging is a plain
+// 16-byte copy.  Kernels are compiled for the block edges 8 and 16 (index
+// arithmetic folds to shifts) and for a runtime edge.
 #include <cstdint>
 
 #include "vet_internal.h"
@@ -28,25 +31,22 @@ template <typename R> using vec2_t = typename Vec2<R>::T;
 
 // exp(-x) and 1 - exp(-x) for the optical depth x >= 0 of one segment, given
 // y = -x log2(e) (segment lengths are stored pre-scaled by -h log2(e)).
-//   FP32: below x = 1/2 both come from the Taylor series of 1 - exp(-x) cut
-//   after x^8 (remainder below x^9/9!, i.e. < 1.4e-8 of the value at 1/2),
-//   which is accurate to rounding where 1 - e would cancel and more accurate
-//   than the MUFU; above it e comes from the MUFU (ex2.approx) and 1 - e is
-//   well conditioned.
+//   FP32: for x < 1/2 both come from a polynomial, 1 - 2^y = y q(y) with q of
+//   degree 5 fitted by weighted least squares (relative error 1.4e-9 in exact
+//   arithmetic, i.e. FP32 rounding dominates), accurate where 1 - e would
+//   cancel and more accurate than the MUFU; for x >= 1/2, e comes from the
+//   MUFU (ex2.approx) and 1 - e is well conditioned.
 //   FP64: the CUDA math library's exp2 and expm1.
 __device__ __forceinline__ void attenuation(float y, float &e, float &om) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
-  const float x = y * -0.6931471805599453f;
-  float p = -2.48015873015873e-05f;             // -1/8!
-  p = fmaf(p, x, 1.984126984126984e-04f);       //  1/7!
-  p = fmaf(p, x, -1.388888888888889e-03f);      // -1/6!
-  p = fmaf(p, x, 8.333333333333333e-03f);       //  1/5!
-  p = fmaf(p, x, -4.166666666666667e-02f);      // -1/4!
-  p = fmaf(p, x, 1.666666666666667e-01f);       //  1/3!
-  p = fmaf(p, x, -0.5f);                        // -1/2!
-  p = fmaf(p, x, 1.0f);
-  p *= x;
-  const bool thin = x < 0.5f;
+  float q = -1.243609540706334e-04f;
+  q = fmaf(q, y, -1.3099410122314181e-03f);
+  q = fmaf(q, y, -9.60941463103728e-03f);
+  q = fmaf(q, y, -5.550262416593144e-02f);
+  q = fmaf(q, y, -2.4022641347108148e-01f);
+  q = fmaf(q, y, -6.931471795930371e-01f);
+  const float p = q * y;
+  const bool thin = y > -0.7213475204444817f;  // x < 1/2
   om = thin ? p : 1.0f - e;
   e = thin ? 1.0f - p : e;
 }
@@ -60,17 +60,32 @@ __device__ __forceinline__ void attenuation(double y, double &e, double &om) {
 // ray's start: after the loop, I(start) = acc + T * I(entry point).
 template <typename R>
 __device__ __forceinline__ void march(const vec2_t<R> *__restrict__ tile, int idx, int last,
-                                      const R *__restrict__ len, const int16_t *__restrict__ delta, R &acc,
-                                      R &T) {
+                                      const TplEvent<R> *__restrict__ ev, R &acc, R &T) {
   acc = R(0);
   T = R(1);
-  for (int e = 0; e <= last; ++e) {
-    const vec2_t<R> ks = tile[idx];
-    R ex, om;
-    attenuation(ks.x * len[e], ex, om);
-    acc = fma(ks.y * om, T, acc);
-    T *= ex;
-    idx += delta[e];
+  int e = 0;
+  for (; e < last; e += 2) {  // two segments per trip
+    const TplEvent<R> e0 = ev[e];
+    const vec2_t<R> k0 = tile[idx];
+    idx += e0.delta;
+    const TplEvent<R> e1 = ev[e + 1];
+    const vec2_t<R> k1 = tile[idx];
+    idx += e1.delta;
+    R x0, o0, x1, o1;
+    attenuation(k0.x * e0.len, x0, o0);
+    attenuation(k1.x * e1.len, x1, o1);
+    acc = fma(k0.y * o0, T, acc);
+    T *= x0;
+    acc = fma(k1.y * o1, T, acc);
+    T *= x1;
+  }
+  if (e == last) {
+    const TplEvent<R> e0 = ev[e];
+    const vec2_t<R> k0 = tile[idx];
+    R x0, o0;
+    attenuation(k0.x * e0.len, x0, o0);
+    acc = fma(k0.y * o0, T, acc);
+    T *= x0;
   }
 }
 
@@ -78,15 +93,13 @@ __device__ __forceinline__ void march(const vec2_t<R> *__restrict__ tile, int id
 template <typename R>
 struct Tpl {
   const TplHead<R> *h;
-  const R *clen, *nlen;
-  const int16_t *cdlt, *ndlt, *cpos, *npos, *ck, *nk;
+  const TplEvent<R> *cev, *nev;
+  const int16_t *cpos, *npos, *ck, *nk;
   const vec2_t<R> *cw, *nw;
   __device__ __forceinline__ Tpl(const unsigned char *base, const TplLayout &L)
       : h(reinterpret_cast<const TplHead<R> *>(base)),
-        clen(reinterpret_cast<const R *>(base + L.clen)),
-        nlen(reinterpret_cast<const R *>(base + L.nlen)),
-        cdlt(reinterpret_cast<const int16_t *>(base + L.cdlt)),
-        ndlt(reinterpret_cast<const int16_t *>(base + L.ndlt)),
+        cev(reinterpret_cast<const TplEvent<R> *>(base + L.cev)),
+        nev(reinterpret_cast<const TplEvent<R> *>(base + L.nev)),
         cpos(reinterpret_cast<const int16_t *>(base + L.cpos)),
         npos(reinterpret_cast<const int16_t *>(base + L.npos)),
         ck(reinterpret_cast<const int16_t *>(base + L.ck)),
@@ -95,78 +108,57 @@ struct Tpl {
         nw(reinterpret_cast<const vec2_t<R> *>(base + L.nw)) {}
 };
 
-// Memory-frame face-node indices and weights along one in-plane axis, from
-// the upwind-frame lower node iup and its weights (f on iup + 1, g = 1 - f on
-// iup).  Exact ties may put the exit point a rounding error outside the face;
-// it is then clamped onto the face edge.
-template <typename R>
-__device__ __forceinline__ void axis_nodes(int iup, R f, R g, int sgn, int B, int &m0, int &m1, R &w0, R &w1) {
-  if (iup < 0) {
-    iup = 0; f = R(0); g = R(1);
-  } else if (iup > B - 1) {
-    iup = B - 1; f = R(1); g = R(0);
-  }
-  m0 = sgn > 0 ? iup : B - iup;
-  m1 = sgn > 0 ? iup + 1 : B - iup - 1;
-  w0 = g;
-  w1 = f;
-}
-
 // Bilinear interpolation on incoming face ae (Sec. 2.2.5 reading: short
-// characteristics between blocks).  l[] are the ray's upwind-frame
-// coordinates, k/w its exit-table rows for the two in-plane axes.
+// characteristics between blocks).  The face is staged in the upwind frame
+// with row stride B + 2 (node B + 1 is zero padding, reached only with weight
+// 0).  lb, lc are the ray's upwind-frame coordinates along the two in-plane
+// axes, kb/kc and wb/wc its exit-table entries (floor and (f, 1-f)).
 template <typename R>
-__device__ __forceinline__ R face_value(const R *__restrict__ fin, int nnode, int B, int ae, const int *sgn,
-                                        int lb, int lc, int kb, int kc, vec2_t<R> wb, vec2_t<R> wc) {
-  const int b = ae == 0 ? 1 : 0, c = ae == 2 ? 1 : 2;
-  int ub0, ub1, vc0, vc1;
-  R gb0, gb1, gc0, gc1;
-  axis_nodes<R>(lb + kb, wb.x, wb.y, sgn[b], B, ub0, ub1, gb0, gb1);
-  axis_nodes<R>(lc + kc, wc.x, wc.y, sgn[c], B, vc0, vc1, gc0, gc1);
-  const R *F = fin + ae * nnode;
-  const int W = B + 1;
-  return gb0 * gc0 * F[ub0 * W + vc0] + gb1 * gc0 * F[ub1 * W + vc0] + gb0 * gc1 * F[ub0 * W + vc1] +
-         gb1 * gc1 * F[ub1 * W + vc1];
+__device__ __forceinline__ R face_value(const R *__restrict__ fin, int fstride, int B, int ae, int lb, int lc,
+                                        int kb, int kc, vec2_t<R> wb, vec2_t<R> wc) {
+  const int W = B + 2;
+  const int ib = max(lb + kb, 0), ic = max(lc + kc, 0);
+  const R *F = fin + ae * fstride + ib * W + ic;
+  return wb.y * (wc.y * F[0] + wc.x * F[1]) + wb.x * (wc.y * F[W] + wc.x * F[W + 1]);
 }
 
-// Copy a direction template into shared memory (16-byte words).
-__device__ __forceinline__ void load_template(unsigned char *dst, const unsigned char *src, int bytes) {
+// Copy `bytes` (a multiple of 16) with the whole CTA.
+__device__ __forceinline__ void cta_copy16(void *dst, const void *src, int bytes) {
   const int4 *s = reinterpret_cast<const int4 *>(src);
   int4 *d = reinterpret_cast<int4 *>(dst);
   for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = s[i];
 }
 
-// The three faces entering block (bx, by, bz) for internal direction d:
-// upwind neighbours' outgoing face nodes, or the constant boundary value.
+// The three faces entering block (bx, by, bz) for internal direction d: the
+// upwind neighbours' stored downwind faces, or the constant boundary value.
 template <typename R>
-__device__ __forceinline__ void load_incoming(R *fin, const GridDims &g, int bx, int by, int bz, int d,
-                                              const TplHead<R> *__restrict__ hd, const R *__restrict__ faces,
-                                              const R *__restrict__ Ib) {
+__device__ __forceinline__ void stage_incoming(R *fin, const GridDims &g, int bx, int by, int bz, int d,
+                                               const TplHead<R> *__restrict__ hd, const R *__restrict__ faces,
+                                               const R *__restrict__ Ib) {
   const int nblk = g.nbx * g.nby * g.nbz;
   const int b3[3] = {bx, by, bz};
   const int nb3[3] = {g.nbx, g.nby, g.nbz};
-  const int ext = hd->ext;
   for (int a = 0; a < 3; ++a) {
     const int s = hd->sgn[a];
     int nb[3] = {b3[0], b3[1], b3[2]};
     nb[a] -= s;
-    R *dst = fin + a * g.nnode;
+    R *dst = fin + a * g.fstride;
     if (nb[a] < 0 || nb[a] >= nb3[a]) {
       const int face = 2 * a + (s > 0 ? 0 : 1);
-      const R v = Ib ? Ib[(long long)face * g.ndir + ext] : R(0);
-      for (int i = threadIdx.x; i < g.nnode; i += blockDim.x) dst[i] = v;
+      const R v = Ib ? Ib[(long long)face * g.ndir + hd->ext] : R(0);
+      for (int i = threadIdx.x; i < g.fstride; i += blockDim.x) dst[i] = v;
     } else {
       const long long nid = ((long long)nb[2] * g.nby + nb[1]) * g.nbx + nb[0];
-      const R *src = faces + (((long long)d * nblk + nid) * 3 + a) * g.nnode;
-      for (int i = threadIdx.x; i < g.nnode; i += blockDim.x) dst[i] = src[i];
+      cta_copy16(dst, faces + (((long long)d * nblk + nid) * 3 + a) * g.fstride, g.fstride * (int)sizeof(R));
     }
   }
 }
 
-template <typename R>
+template <typename R, int BC>
 __device__ __forceinline__ void load_tile(vec2_t<R> *tile, const GridDims &g, int bx, int by, int bz,
                                           const R *__restrict__ kappa, const R *__restrict__ S) {
-  const int B = g.B, B2 = B * B, B3 = B2 * B;
+  const int B = BC ? BC : g.B;
+  const int B2 = B * B, B3 = B2 * B;
   for (int i = threadIdx.x; i < B3; i += blockDim.x) {
     const int x = i % B, y = (i / B) % B, z = i / B2;
     const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
@@ -179,68 +171,76 @@ __device__ __forceinline__ void load_tile(vec2_t<R> *tile, const GridDims &g, in
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Dynamic shared memory of a CTA that stages `dt` directions at a time.
 template <typename R>
-__host__ __device__ inline size_t smem_bytes(int B, int nnode) {
-  return align16(sizeof(vec2_t<R>) * (size_t)B * B * B) + align16(sizeof(R) * 3 * (size_t)nnode) +
-         (size_t)tpl_layout<R>(B).bytes;
+__host__ __device__ inline size_t smem_bytes(int B, int dt) {
+  return align16(sizeof(vec2_t<R>) * (size_t)B * B * B) +
+         (size_t)dt * (sizeof(R) * 3 * (size_t)face_stride_elems<R>(B) + (size_t)tpl_layout<R>(B).bytes);
+}
+
+constexpr int kDirTile = 8;   // directions staged per cell-pass tile
+constexpr size_t kSmemMax = 232448;
+
+template <typename R>
+int cell_dir_tile(int B) {
+  int dt = kDirTile;
+  while (dt > 1 && smem_bytes<R>(B, dt) > kSmemMax) --dt;
+  return dt;
 }
 
 // ---------------------------------------------------------------- face pass
-template <typename R>
+template <typename R, int BC>
 __global__ void __launch_bounds__(256) face_pass_kernel(GridDims g, const R *__restrict__ kappa,
                                                         const R *__restrict__ S, const R *__restrict__ Ib,
                                                         const unsigned char *__restrict__ tpl_g,
                                                         const FaceItem *__restrict__ items, R *__restrict__ faces) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int B = g.B;
+  const int B = BC ? BC : g.B;
+  const int W = B + 2, N1 = B + 1, NN = N1 * N1;
   const TplLayout TL = tpl_layout<R>(B);
   vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
   R *fin = reinterpret_cast<R *>(smem + align16(sizeof(vec2_t<R>) * (size_t)B * B * B));
-  unsigned char *tb = reinterpret_cast<unsigned char *>(fin) + align16(sizeof(R) * 3 * (size_t)g.nnode);
+  unsigned char *tb = reinterpret_cast<unsigned char *>(fin + 3 * g.fstride);
   const Tpl<R> T(tb, TL);
   const FaceItem it = items[blockIdx.x];
   const int bx = it.block % g.nbx, by = (it.block / g.nbx) % g.nby, bz = it.block / (g.nbx * g.nby);
   const int nblk = g.nbx * g.nby * g.nbz;
-  load_tile<R>(tile, g, bx, by, bz, kappa, S);
-  const int nn3 = 3 * g.nnode;
+  load_tile<R, BC>(tile, g, bx, by, bz, kappa, S);
   for (int d = it.dir_begin; d < it.dir_begin + it.dir_count; ++d) {
+    const unsigned char *src = tpl_g + (size_t)d * TL.bytes;
     __syncthreads();
-    load_template(tb, tpl_g + (size_t)d * TL.bytes, TL.bytes);
-    load_incoming<R>(fin, g, bx, by, bz, d, reinterpret_cast<const TplHead<R> *>(tpl_g + (size_t)d * TL.bytes),
-                     faces, Ib);
+    cta_copy16(tb, src, TL.bytes);
+    stage_incoming<R>(fin, g, bx, by, bz, d, reinterpret_cast<const TplHead<R> *>(src), faces, Ib);
     __syncthreads();
     const int sgn[3] = {T.h->sgn[0], T.h->sgn[1], T.h->sgn[2]};
-    R *out = faces + ((long long)d * nblk + it.block) * 3 * g.nnode;
-    for (int j = threadIdx.x; j < nn3; j += blockDim.x) {
-      const int a = j / g.nnode, r = j - a * g.nnode;
-      const int u = r / (B + 1), v = r - u * (B + 1);
+    R *out = faces + ((long long)d * nblk + it.block) * 3 * g.fstride;
+    for (int j = threadIdx.x; j < 3 * NN; j += blockDim.x) {
+      const int a = j / NN, r = j - a * NN;
+      const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
       const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-      int P[3];
-      P[a] = sgn[a] > 0 ? B : 0;  // memory-frame node position
-      P[b] = u;
-      P[c] = v;
-      int L[3], cell[3];
-      for (int q = 0; q < 3; ++q) {
-        L[q] = sgn[q] > 0 ? P[q] : B - P[q];        // upwind-frame position
-        cell[q] = sgn[q] > 0 ? L[q] - 1 : B - L[q];  // memory-frame start cell
-      }
+      int L[3];
+      L[a] = B;
+      L[b] = ub;
+      L[c] = uc;
       int last = T.npos[L[0]], ae = 0;
-      if (T.npos[(B + 1) + L[1]] < last) { last = T.npos[(B + 1) + L[1]]; ae = 1; }
-      if (T.npos[2 * (B + 1) + L[2]] < last) { last = T.npos[2 * (B + 1) + L[2]]; ae = 2; }
+      if (T.npos[N1 + L[1]] < last) { last = T.npos[N1 + L[1]]; ae = 1; }
+      if (T.npos[2 * N1 + L[2]] < last) { last = T.npos[2 * N1 + L[2]]; ae = 2; }
       R acc = R(0), Tr = R(1);
-      if (last >= 0) march<R>(tile, cell[0] + B * (cell[1] + B * cell[2]), last, T.nlen, T.ndlt, acc, Tr);
+      if (last >= 0) {  // then every L >= 1 and the start cell is inside the block
+        int cell[3];
+        for (int q = 0; q < 3; ++q) cell[q] = sgn[q] > 0 ? L[q] - 1 : B - L[q];
+        march<R>(tile, cell[0] + B * (cell[1] + B * cell[2]), last, T.nev, acc, Tr);
+      }
       const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
-      const int row = (ae * 2) * (B + 1) + L[ae];
-      const R Iin = face_value<R>(fin, g.nnode, B, ae, sgn, L[eb], L[ec], T.nk[row], T.nk[row + (B + 1)],
-                                  T.nw[row], T.nw[row + (B + 1)]);
-      out[j] = fma(Tr, Iin, acc);
+      const int row = (ae * 2) * N1 + L[ae];
+      const R Iin = face_value<R>(fin, g.fstride, B, ae, L[eb], L[ec], T.nk[row], T.nk[row + N1], T.nw[row],
+                                  T.nw[row + N1]);
+      out[a * g.fstride + ub * W + uc] = fma(Tr, Iin, acc);
     }
   }
 }
 
 // ---------------------------------------------------------------- cell pass
-constexpr int kCPT = 2;  // cells per thread
-
 __device__ __forceinline__ void atomic_max_nonneg(void *p, float v) {
   atomicMax(reinterpret_cast<unsigned int *>(p), __float_as_uint(v));
 }
@@ -248,118 +248,109 @@ __device__ __forceinline__ void atomic_max_nonneg(void *p, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(v));
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(512) cell_pass_kernel(GridDims g, int parts, const R *__restrict__ kappa,
-                                                        const R *__restrict__ S, const R *__restrict__ Ib,
-                                                        const unsigned char *__restrict__ tpl_g,
-                                                        const R *__restrict__ faces, R *__restrict__ I_out,
-                                                        R *__restrict__ M_out, R *__restrict__ E_out,
-                                                        R *__restrict__ f_out, void *emax_bits) {
+constexpr int kCellThreads = 512;  // one cell per thread
+
+// Cell pass: one CTA per (block, slab of up to 512 of the block's cells), one
+// cell per thread; all directions are visited in tiles of `dt` (templates and
+// incoming faces of a whole tile are staged at once, so warps synchronise once
+// per tile, not per direction).
+template <typename R, int MODE, int BC>
+__global__ void __launch_bounds__(kCellThreads, 2)
+    cell_pass_kernel(GridDims g, int parts, int dt, const R *__restrict__ kappa, const R *__restrict__ S,
+                     const R *__restrict__ Ib, const unsigned char *__restrict__ tpl_g, const R *__restrict__ faces,
+                     R *__restrict__ I_out, R *__restrict__ M_out, R *__restrict__ E_out, R *__restrict__ f_out,
+                     void *emax_bits) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int B = g.B, B2 = B * B, B3 = B2 * B;
+  const int B = BC ? BC : g.B;
+  const int B2 = B * B, B3 = B2 * B;
   const TplLayout TL = tpl_layout<R>(B);
+  const int fstride = g.fstride;
+  const size_t fbytes = sizeof(R) * 3 * (size_t)fstride;
   vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
-  R *fin = reinterpret_cast<R *>(smem + align16(sizeof(vec2_t<R>) * (size_t)B3));
-  unsigned char *tb = reinterpret_cast<unsigned char *>(fin) + align16(sizeof(R) * 3 * (size_t)g.nnode);
-  const Tpl<R> T(tb, TL);
+  unsigned char *fin_base = smem + align16(sizeof(vec2_t<R>) * (size_t)B3);
+  unsigned char *tb_base = fin_base + fbytes * dt;
   const int blk = blockIdx.x / parts, part = blockIdx.x - blk * parts;
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
   const int cpc = B3 / parts;  // cells of this CTA
-  load_tile<R>(tile, g, bx, by, bz, kappa, S);
+  load_tile<R, BC>(tile, g, bx, by, bz, kappa, S);
 
-  int lc[kCPT];        // local cell index in the block, or -1
-  long long gc[kCPT];  // global cell index
-  for (int i = 0; i < kCPT; ++i) {
-    const int k = threadIdx.x + i * blockDim.x;
-    lc[i] = k < cpc ? part * cpc + k : -1;
-    const int c = lc[i] < 0 ? 0 : lc[i];
-    const int x = c % B, y = (c / B) % B, z = c / B2;
-    gc[i] = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
-  }
+  const bool active = (int)threadIdx.x < cpc;
+  const int lc = part * cpc + (active ? (int)threadIdx.x : 0);  // local cell index in the block
+  const int cx = lc % B, cy = (lc / B) % B, cz = lc / B2;
+  const long long gc = ((long long)(bz * B + cz) * g.ny + (by * B + cy)) * g.nx + (bx * B + cx);
   // Moments accumulated over all directions.  E, Pxx, Pyy and Pzz (sums of
   // positive terms that f_ii = P_ii / E depends on) carry a Kahan
   // compensation term: plain sequential FP32 sums of N terms lose about
   // N/2 ulp, which would dominate the error of f.
-  R mom[MODE == 0 ? kCPT : 1][10];
-  R cmp[MODE == 0 ? kCPT : 1][4];
-  if (MODE == 0) {
-    for (int i = 0; i < kCPT; ++i) {
-      for (int m = 0; m < 10; ++m) mom[i][m] = R(0);
-      for (int m = 0; m < 4; ++m) cmp[i][m] = R(0);
-    }
-  }
+  R mom[10], cmp[4];
+  for (int m = 0; m < 10; ++m) mom[m] = R(0);
+  for (int m = 0; m < 4; ++m) cmp[m] = R(0);
 
-  for (int d = 0; d < g.ndir; ++d) {
+  for (int d0 = 0; d0 < g.ndir; d0 += dt) {
+    const int nd = min(dt, g.ndir - d0);
     __syncthreads();
-    load_template(tb, tpl_g + (size_t)d * TL.bytes, TL.bytes);
-    load_incoming<R>(fin, g, bx, by, bz, d, reinterpret_cast<const TplHead<R> *>(tpl_g + (size_t)d * TL.bytes),
-                     faces, Ib);
+    cta_copy16(tb_base, tpl_g + (size_t)d0 * TL.bytes, nd * TL.bytes);
+    for (int j = 0; j < nd; ++j)
+      stage_incoming<R>(reinterpret_cast<R *>(fin_base + fbytes * j), g, bx, by, bz, d0 + j,
+                        reinterpret_cast<const TplHead<R> *>(tpl_g + (size_t)(d0 + j) * TL.bytes), faces, Ib);
     __syncthreads();
-    const int sgn[3] = {T.h->sgn[0], T.h->sgn[1], T.h->sgn[2]};
-    R coef[10];  // w (1, n, n n) of this direction
-    {
-      const R w = T.h->w, nx = T.h->n[0], ny = T.h->n[1], nz = T.h->n[2];
-      coef[0] = w; coef[1] = w * nx; coef[2] = w * ny; coef[3] = w * nz;
-      coef[4] = coef[1] * nx; coef[5] = coef[2] * ny; coef[6] = coef[3] * nz;
-      coef[7] = coef[1] * ny; coef[8] = coef[1] * nz; coef[9] = coef[2] * nz;
-    }
-#pragma unroll
-    for (int i = 0; i < kCPT; ++i) {
-      if (lc[i] < 0) continue;
-      const int c = lc[i];
-      const int x = c % B, y = (c / B) % B, z = c / B2;
+    if (!active) continue;
+    for (int j = 0; j < nd; ++j) {
+      const Tpl<R> T(tb_base + (size_t)j * TL.bytes, TL);
+      const R *fin = reinterpret_cast<const R *>(fin_base + fbytes * j);
       int l[3];
-      l[0] = sgn[0] > 0 ? x : B - 1 - x;
-      l[1] = sgn[1] > 0 ? y : B - 1 - y;
-      l[2] = sgn[2] > 0 ? z : B - 1 - z;
+      l[0] = T.h->sgn[0] > 0 ? cx : B - 1 - cx;
+      l[1] = T.h->sgn[1] > 0 ? cy : B - 1 - cy;
+      l[2] = T.h->sgn[2] > 0 ? cz : B - 1 - cz;
       int last = T.cpos[l[0]], ae = 0;
       if (T.cpos[B + l[1]] < last) { last = T.cpos[B + l[1]]; ae = 1; }
       if (T.cpos[2 * B + l[2]] < last) { last = T.cpos[2 * B + l[2]]; ae = 2; }
       R acc, Tr;
-      march<R>(tile, c, last, T.clen, T.cdlt, acc, Tr);
+      march<R>(tile, lc, last, T.cev, acc, Tr);
       const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
       const int row = (ae * 2) * B + l[ae];
-      const R Iin = face_value<R>(fin, g.nnode, B, ae, sgn, l[eb], l[ec], T.ck[row], T.ck[row + B], T.cw[row],
+      const R Iin = face_value<R>(fin, fstride, B, ae, l[eb], l[ec], T.ck[row], T.ck[row + B], T.cw[row],
                                   T.cw[row + B]);
       const R I = fma(Tr, Iin, acc);
       if (MODE == 1) {
-        I_out[(long long)T.h->ext * g.ncell + gc[i]] = I;
+        I_out[(long long)T.h->ext * g.ncell + gc] = I;
       } else {
+        const R w = T.h->w, nx = T.h->n[0], ny = T.h->n[1], nz = T.h->n[2];
+        const R wI = w * I, wIx = wI * nx, wIy = wI * ny, wIz = wI * nz;
+        const R term[4] = {wI, wIx * nx, wIy * ny, wIz * nz};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {  // E, Pxx, Pyy, Pzz: compensated
           const int m = q == 0 ? 0 : 3 + q;
-          const R y = I * coef[m] - cmp[i][q];
-          const R t = mom[i][m] + y;
-          cmp[i][q] = (t - mom[i][m]) - y;
-          mom[i][m] = t;
+          const R y = term[q] - cmp[q];
+          const R t = mom[m] + y;
+          cmp[q] = (t - mom[m]) - y;
+          mom[m] = t;
         }
-        mom[i][1] = fma(I, coef[1], mom[i][1]);
-        mom[i][2] = fma(I, coef[2], mom[i][2]);
-        mom[i][3] = fma(I, coef[3], mom[i][3]);
-        mom[i][7] = fma(I, coef[7], mom[i][7]);
-        mom[i][8] = fma(I, coef[8], mom[i][8]);
-        mom[i][9] = fma(I, coef[9], mom[i][9]);
+        mom[1] += wIx;
+        mom[2] += wIy;
+        mom[3] += wIz;
+        mom[7] = fma(wIx, ny, mom[7]);
+        mom[8] = fma(wIx, nz, mom[8]);
+        mom[9] = fma(wIy, nz, mom[9]);
       }
     }
   }
   if (MODE == 0) {
     R emax = R(0);
-    for (int i = 0; i < kCPT; ++i) {
-      if (lc[i] < 0) continue;
-      const long long c = gc[i];
-      const R E = mom[i][0];
+    if (active) {
+      const R E = mom[0];
       if (M_out) {
-        for (int m = 0; m < 10; ++m) M_out[m * g.ncell + c] = mom[i][m];
+        for (int m = 0; m < 10; ++m) M_out[m * g.ncell + gc] = mom[m];
       } else {
-        E_out[c] = E;
+        E_out[gc] = E;
       }
       if (E > R(0)) {
         const R inv = R(1) / E;
-        for (int m = 0; m < 6; ++m) f_out[m * g.ncell + c] = mom[i][4 + m] * inv;
+        for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = mom[4 + m] * inv;
       } else {
-        for (int m = 0; m < 6; ++m) f_out[m * g.ncell + c] = m < 3 ? R(1) / R(3) : R(0);
+        for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = m < 3 ? R(1) / R(3) : R(0);
       }
-      emax = E > emax ? E : emax;
+      emax = E;
     }
     for (int o = 16; o > 0; o >>= 1) {
       const R v = __shfl_xor_sync(0xffffffffu, emax, o);
@@ -414,22 +405,56 @@ __global__ void __launch_bounds__(256) moments_kernel(long long ncell, int ndir,
     for (int m = 0; m < 10; ++m) M[m * ncell + c] = acc[m];
 }
 
-}  // namespace
-
-static int cell_parts(int B) {
+int cell_parts(int B) {
   const int B3 = B * B * B;
-  int parts = (B3 + 1023) / 1024;
+  int parts = (B3 + kCellThreads - 1) / kCellThreads;
   while (B3 % parts) ++parts;
   return parts;
 }
+
+template <typename R, int BC>
+void face_launch(const GridDims &g, const R *kappa, const R *S, const R *Ib, const unsigned char *tpl,
+                 const FaceItem *items, int nitems, R *faces, cudaStream_t st) {
+  face_pass_kernel<R, BC><<<nitems, 256, smem_bytes<R>(g.B, 1), st>>>(g, kappa, S, Ib, tpl, items, faces);
+}
+
+template <typename R, int MODE, int BC>
+void cell_launch(const GridDims &g, const R *kappa, const R *S, const R *Ib, const unsigned char *tpl,
+                 const R *faces, R *I_out, R *M_out, R *E_out, R *f_out, void *emax_bits, cudaStream_t st) {
+  const int parts = cell_parts(g.B);
+  const int cpc = g.B * g.B * g.B / parts;
+  const int threads = (cpc + 31) / 32 * 32;
+  const int nblk = g.nbx * g.nby * g.nbz;
+  const int dt = cell_dir_tile<R>(g.B);
+  cell_pass_kernel<R, MODE, BC><<<nblk * parts, threads, smem_bytes<R>(g.B, dt), st>>>(
+      g, parts, dt, kappa, S, Ib, tpl, faces, I_out, M_out, E_out, f_out, emax_bits);
+}
+
+template <typename R>
+cudaError_t set_smem_attrs() {
+  const int lim = (int)kSmemMax;
+  const void *fns[] = {(const void *)face_pass_kernel<R, 8>,       (const void *)face_pass_kernel<R, 16>,
+                       (const void *)face_pass_kernel<R, 0>,       (const void *)cell_pass_kernel<R, 0, 8>,
+                       (const void *)cell_pass_kernel<R, 0, 16>,   (const void *)cell_pass_kernel<R, 0, 0>,
+                       (const void *)cell_pass_kernel<R, 1, 8>,    (const void *)cell_pass_kernel<R, 1, 16>,
+                       (const void *)cell_pass_kernel<R, 1, 0>};
+  for (const void *f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
 
 template <typename R>
 cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, const R *Ib,
                               const unsigned char *tpl, const FaceItem *items, int nitems, R *faces,
                               cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  const size_t sm = smem_bytes<R>(g.B, g.nnode);
-  face_pass_kernel<R><<<nitems, 256, sm, st>>>(g, kappa, S, Ib, tpl, items, faces);
+  if (g.B == 16) face_launch<R, 16>(g, kappa, S, Ib, tpl, items, nitems, faces, st);
+  else if (g.B == 8) face_launch<R, 8>(g, kappa, S, Ib, tpl, items, nitems, faces, st);
+  else face_launch<R, 0>(g, kappa, S, Ib, tpl, items, nitems, faces, st);
   return cudaGetLastError();
 }
 
@@ -437,19 +462,18 @@ template <typename R>
 cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const R *Ib,
                              const unsigned char *tpl, const R *faces, R *I_out, R *M_out, R *E_out,
                              R *f_out, void *emax_bits, cudaStream_t st) {
-  const int parts = cell_parts(g.B);
-  const int cpc = g.B * g.B * g.B / parts;
-  int threads = (cpc + kCPT - 1) / kCPT;
-  threads = (threads + 31) / 32 * 32;
-  const int nblk = g.nbx * g.nby * g.nbz;
-  const size_t sm = smem_bytes<R>(g.B, g.nnode);
+#define VET_CELL(MODE, BC) \
+  cell_launch<R, MODE, BC>(g, kappa, S, Ib, tpl, faces, I_out, M_out, E_out, f_out, emax_bits, st)
   if (mode == 0) {
-    cell_pass_kernel<R, 0><<<nblk * parts, threads, sm, st>>>(g, parts, kappa, S, Ib, tpl, faces, I_out, M_out,
-                                                               E_out, f_out, emax_bits);
+    if (g.B == 16) VET_CELL(0, 16);
+    else if (g.B == 8) VET_CELL(0, 8);
+    else VET_CELL(0, 0);
   } else {
-    cell_pass_kernel<R, 1><<<nblk * parts, threads, sm, st>>>(g, parts, kappa, S, Ib, tpl, faces, I_out, M_out,
-                                                               E_out, f_out, emax_bits);
+    if (g.B == 16) VET_CELL(1, 16);
+    else if (g.B == 8) VET_CELL(1, 8);
+    else VET_CELL(1, 0);
   }
+#undef VET_CELL
   return cudaGetLastError();
 }
 
@@ -474,28 +498,23 @@ cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef,
 }
 
 size_t pass_smem_bytes(int B, int nnode, bool fp64) {
-  return fp64 ? smem_bytes<double>(B, nnode) : smem_bytes<float>(B, nnode);
+  (void)nnode;
+  return fp64 ? smem_bytes<double>(B, 1) : smem_bytes<float>(B, 1);
 }
 
 // Opt the shared-memory-heavy kernels in to the full 227 KB per CTA on the
 // current device (the attribute is per device and function).
 cudaError_t prepare_kernels() {
-  const int lim = 232448;
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(face_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(face_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(cell_pass_kernel<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(cell_pass_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(cell_pass_kernel<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(cell_pass_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  return cudaSuccess;
+  cudaError_t e = set_smem_attrs<float>();
+  if (e != cudaSuccess) return e;
+  return set_smem_attrs<double>();
 }
 
 #define VET_INSTANTIATE(R)                                                                                      \
   template cudaError_t launch_face_level<R>(const GridDims &, const R *, const R *, const R *,                \
-                                            const unsigned char *, const FaceItem *, int, R *, cudaStream_t); \
+                                            const unsigned char *, const FaceItem *, int, R *, cudaStream_t);  \
   template cudaError_t launch_cell_pass<R>(const GridDims &, int, const R *, const R *, const R *,            \
-                                           const unsigned char *, const R *, R *, R *, R *, R *, void *,        \
+                                           const unsigned char *, const R *, R *, R *, R *, R *, void *,       \
                                            cudaStream_t);                                                       \
   template cudaError_t launch_floor_fix<R>(long long, const R *, long long, const void *, double, R *,        \
                                            cudaStream_t);                                                       \
