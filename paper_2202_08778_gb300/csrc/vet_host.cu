@@ -157,7 +157,7 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   }
   hd->w = R(d[3]);
   hd->ext = ext;
-  const int stride[3] = {1, B, B * B};
+  const int stride[3] = {1, vet::tile_stride_y(B), vet::tile_stride_z(B)};
   // cell rays: planes at t = (m + 1/2)/|n_a|, m = 0..B-1
   std::vector<Event> ev;
   for (int a = 0; a < 3; ++a)
@@ -280,7 +280,7 @@ vet_status build_context(vet_ctx *c) {
   c->face_segs = ns_tot * c->nblk;
   // face-pass schedule: level L of a block in octant o is its upwind-ordered
   // index sum; one item = (block, up to kGroup directions of one octant).
-  const int kGroup = 4;
+  const int kGroup = vet::kFaceGroup;
   const int nb[3] = {c->dims.nbx, c->dims.nby, c->dims.nbz};
   c->nlevels = nb[0] + nb[1] + nb[2] - 2;
   std::vector<std::vector<FaceItem>> per_level(c->nlevels);
@@ -457,7 +457,8 @@ vet_status run_face_pass(vet_ctx *c, const R *kappa, const R *S, const R *Ib, cu
   for (int L = 0; L < c->nlevels; ++L) {
     const int n = c->level_off[L + 1] - c->level_off[L];
     cudaError_t e = vet::launch_face_level<R>(c->dims, kappa, S, Ib, (const unsigned char *)c->d_tpl,
-                                               c->d_items + c->level_off[L], n, (R *)c->d_faces, st);
+                                               c->d_items + c->level_off[L], n, vet::kFaceGroup, (R *)c->d_faces,
+                                               st);
     if (e) return cuda_err(c, e, "face pass launch");
   }
   return VET_OK;
@@ -571,7 +572,7 @@ VET_API vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_con
   if (!(qn > 1e-12) || !std::isfinite(qn)) return set_err(nullptr, VET_EINVAL, "rotation quaternion is zero or not finite");
   const bool fp64 = cfg->precision == VET_FP64;
   const int nnode = (g.block + 1) * (g.block + 1);
-  if (vet::pass_smem_bytes(g.block, nnode, fp64) > 232448)
+  if (vet::pass_smem_bytes(g.block, vet::kFaceGroup, fp64) > 232448)
     return set_err(nullptr, VET_EUNSUPPORTED, "block edge too large for one CTA's shared memory at this precision");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {

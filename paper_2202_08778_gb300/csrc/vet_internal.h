@@ -91,6 +91,14 @@ struct GridDims {
   long long ncell;    // nx*ny*nz
 };
 
+// Shared-memory kappa/S tile of a block: cell (x, y, z) at
+// x + (B+1) y + (B+1)^2 z.  All three strides are odd, so any uniform shift of
+// a warp's 8-byte accesses along a row, column or pillar of the block is free
+// of bank conflicts.
+__host__ __device__ inline int tile_stride_y(int B) { return B + 1; }
+__host__ __device__ inline int tile_stride_z(int B) { return (B + 1) * (B + 1); }
+__host__ __device__ inline int tile_elems(int B) { return (B + 1) * (B + 1) * B; }
+
 // Stored faces: node (ub, uc) of a face, in the upwind frame of the direction
 // (the in-plane axes flipped where the direction component is negative), at
 // ub * (B + 2) + uc; row and column B + 1 are zero padding.
@@ -111,9 +119,11 @@ struct FaceItem {
 
 // Launchers (vet_kernels.cu).  All return the cudaGetLastError() of the
 // launch.  R = float or double.
+// Face pass of one wavefront level: nitems items of at most max_dirs
+// directions each.
 template <typename R>
 cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, const R *Ib,
-                              const unsigned char *tpl, const FaceItem *items, int nitems, R *faces,
+                              const unsigned char *tpl, const FaceItem *items, int nitems, int max_dirs, R *faces,
                               cudaStream_t st);
 
 // mode 0: moments + f (+ E for the floor rule); mode 1: write I_out.
@@ -130,8 +140,11 @@ template <typename R>
 cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef, R *M_out,
                            cudaStream_t st);
 
-// Dynamic shared memory of one face-pass or cell-pass CTA.
-size_t pass_smem_bytes(int B, int nnode, bool fp64);
+// Dynamic shared memory of a CTA staging `dirs` directions.
+size_t pass_smem_bytes(int B, int dirs, bool fp64);
+
+// Directions per face-pass item.
+constexpr int kFaceGroup = 4;
 
 // Per-device kernel attributes; call with the context's device current.
 cudaError_t prepare_kernels();

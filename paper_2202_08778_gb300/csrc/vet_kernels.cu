@@ -159,13 +159,14 @@ __device__ __forceinline__ void load_tile(vec2_t<R> *tile, const GridDims &g, in
                                           const R *__restrict__ kappa, const R *__restrict__ S) {
   const int B = BC ? BC : g.B;
   const int B2 = B * B, B3 = B2 * B;
+  const int TY = tile_stride_y(B), TZ = tile_stride_z(B);
   for (int i = threadIdx.x; i < B3; i += blockDim.x) {
     const int x = i % B, y = (i / B) % B, z = i / B2;
     const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
     vec2_t<R> v;
     v.x = kappa[gi];
     v.y = S[gi];
-    tile[i] = v;
+    tile[x + TY * y + TZ * z] = v;
   }
 }
 
@@ -174,7 +175,7 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size
 // Dynamic shared memory of a CTA that stages `dt` directions at a time.
 template <typename R>
 __host__ __device__ inline size_t smem_bytes(int B, int dt) {
-  return align16(sizeof(vec2_t<R>) * (size_t)B * B * B) +
+  return align16(sizeof(vec2_t<R>) * (size_t)tile_elems(B)) +
          (size_t)dt * (sizeof(R) * 3 * (size_t)face_stride_elems<R>(B) + (size_t)tpl_layout<R>(B).bytes);
 }
 
@@ -189,54 +190,62 @@ int cell_dir_tile(int B) {
 }
 
 // ---------------------------------------------------------------- face pass
+constexpr int kFaceThreads = 512;
+
+// Face pass: one CTA per item (a block and up to `dt` directions of one
+// octant at the same wavefront level).  The item's templates and incoming
+// faces are staged at once, then the (direction, node) rays are spread over
+// the CTA's threads.
 template <typename R, int BC>
-__global__ void __launch_bounds__(256) face_pass_kernel(GridDims g, const R *__restrict__ kappa,
-                                                        const R *__restrict__ S, const R *__restrict__ Ib,
-                                                        const unsigned char *__restrict__ tpl_g,
-                                                        const FaceItem *__restrict__ items, R *__restrict__ faces) {
+__global__ void __launch_bounds__(kFaceThreads, 2)
+    face_pass_kernel(GridDims g, const R *__restrict__ kappa, const R *__restrict__ S, const R *__restrict__ Ib,
+                     const unsigned char *__restrict__ tpl_g, const FaceItem *__restrict__ items,
+                     R *__restrict__ faces) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int B = BC ? BC : g.B;
-  const int W = B + 2, N1 = B + 1, NN = N1 * N1;
+  const int W = B + 2, N1 = B + 1, NN = N1 * N1, NN3 = 3 * NN;
+  const int TY = tile_stride_y(B), TZ = tile_stride_z(B);
   const TplLayout TL = tpl_layout<R>(B);
-  vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
-  R *fin = reinterpret_cast<R *>(smem + align16(sizeof(vec2_t<R>) * (size_t)B * B * B));
-  unsigned char *tb = reinterpret_cast<unsigned char *>(fin + 3 * g.fstride);
-  const Tpl<R> T(tb, TL);
+  const size_t fbytes = sizeof(R) * 3 * (size_t)g.fstride;
   const FaceItem it = items[blockIdx.x];
+  vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
+  unsigned char *fin_base = smem + align16(sizeof(vec2_t<R>) * (size_t)tile_elems(B));
+  unsigned char *tb_base = fin_base + fbytes * it.dir_count;
   const int bx = it.block % g.nbx, by = (it.block / g.nbx) % g.nby, bz = it.block / (g.nbx * g.nby);
   const int nblk = g.nbx * g.nby * g.nbz;
   load_tile<R, BC>(tile, g, bx, by, bz, kappa, S);
-  for (int d = it.dir_begin; d < it.dir_begin + it.dir_count; ++d) {
-    const unsigned char *src = tpl_g + (size_t)d * TL.bytes;
-    __syncthreads();
-    cta_copy16(tb, src, TL.bytes);
-    stage_incoming<R>(fin, g, bx, by, bz, d, reinterpret_cast<const TplHead<R> *>(src), faces, Ib);
-    __syncthreads();
-    const int sgn[3] = {T.h->sgn[0], T.h->sgn[1], T.h->sgn[2]};
-    R *out = faces + ((long long)d * nblk + it.block) * 3 * g.fstride;
-    for (int j = threadIdx.x; j < 3 * NN; j += blockDim.x) {
-      const int a = j / NN, r = j - a * NN;
-      const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
-      const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-      int L[3];
-      L[a] = B;
-      L[b] = ub;
-      L[c] = uc;
-      int last = T.npos[L[0]], ae = 0;
-      if (T.npos[N1 + L[1]] < last) { last = T.npos[N1 + L[1]]; ae = 1; }
-      if (T.npos[2 * N1 + L[2]] < last) { last = T.npos[2 * N1 + L[2]]; ae = 2; }
-      R acc = R(0), Tr = R(1);
-      if (last >= 0) {  // then every L >= 1 and the start cell is inside the block
-        int cell[3];
-        for (int q = 0; q < 3; ++q) cell[q] = sgn[q] > 0 ? L[q] - 1 : B - L[q];
-        march<R>(tile, cell[0] + B * (cell[1] + B * cell[2]), last, T.nev, acc, Tr);
-      }
-      const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
-      const int row = (ae * 2) * N1 + L[ae];
-      const R Iin = face_value<R>(fin, g.fstride, B, ae, L[eb], L[ec], T.nk[row], T.nk[row + N1], T.nw[row],
-                                  T.nw[row + N1]);
-      out[a * g.fstride + ub * W + uc] = fma(Tr, Iin, acc);
+  cta_copy16(tb_base, tpl_g + (size_t)it.dir_begin * TL.bytes, it.dir_count * TL.bytes);
+  for (int j = 0; j < it.dir_count; ++j)
+    stage_incoming<R>(reinterpret_cast<R *>(fin_base + fbytes * j), g, bx, by, bz, it.dir_begin + j,
+                      reinterpret_cast<const TplHead<R> *>(tpl_g + (size_t)(it.dir_begin + j) * TL.bytes), faces,
+                      Ib);
+  __syncthreads();
+  for (int w = threadIdx.x; w < it.dir_count * NN3; w += blockDim.x) {
+    const int j = w / NN3, n = w - j * NN3;
+    const Tpl<R> T(tb_base + (size_t)j * TL.bytes, TL);
+    const R *fin = reinterpret_cast<const R *>(fin_base + fbytes * j);
+    const int a = n / NN, r = n - a * NN;
+    const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
+    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+    int L[3];
+    L[a] = B;
+    L[b] = ub;
+    L[c] = uc;
+    int last = T.npos[L[0]], ae = 0;
+    if (T.npos[N1 + L[1]] < last) { last = T.npos[N1 + L[1]]; ae = 1; }
+    if (T.npos[2 * N1 + L[2]] < last) { last = T.npos[2 * N1 + L[2]]; ae = 2; }
+    R acc = R(0), Tr = R(1);
+    if (last >= 0) {  // then every L >= 1 and the start cell is inside the block
+      int cell[3];
+      for (int q = 0; q < 3; ++q) cell[q] = T.h->sgn[q] > 0 ? L[q] - 1 : B - L[q];
+      march<R>(tile, cell[0] + TY * cell[1] + TZ * cell[2], last, T.nev, acc, Tr);
     }
+    const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
+    const int row = (ae * 2) * N1 + L[ae];
+    const R Iin = face_value<R>(fin, g.fstride, B, ae, L[eb], L[ec], T.nk[row], T.nk[row + N1], T.nw[row],
+                                T.nw[row + N1]);
+    faces[(((long long)(it.dir_begin + j) * nblk + it.block) * 3 + a) * g.fstride + ub * W + uc] =
+        fma(Tr, Iin, acc);
   }
 }
 
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(kCellThreads, 2)
   const int fstride = g.fstride;
   const size_t fbytes = sizeof(R) * 3 * (size_t)fstride;
   vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
-  unsigned char *fin_base = smem + align16(sizeof(vec2_t<R>) * (size_t)B3);
+  unsigned char *fin_base = smem + align16(sizeof(vec2_t<R>) * (size_t)tile_elems(B));
   unsigned char *tb_base = fin_base + fbytes * dt;
   const int blk = blockIdx.x / parts, part = blockIdx.x - blk * parts;
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
@@ -277,6 +286,7 @@ __global__ void __launch_bounds__(kCellThreads, 2)
   const bool active = (int)threadIdx.x < cpc;
   const int lc = part * cpc + (active ? (int)threadIdx.x : 0);  // local cell index in the block
   const int cx = lc % B, cy = (lc / B) % B, cz = lc / B2;
+  const int tc = cx + tile_stride_y(B) * cy + tile_stride_z(B) * cz;  // tile index
   const long long gc = ((long long)(bz * B + cz) * g.ny + (by * B + cy)) * g.nx + (bx * B + cx);
   // Moments accumulated over all directions.  E, Pxx, Pyy and Pzz (sums of
   // positive terms that f_ii = P_ii / E depends on) carry a Kahan
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(kCellThreads, 2)
       if (T.cpos[B + l[1]] < last) { last = T.cpos[B + l[1]]; ae = 1; }
       if (T.cpos[2 * B + l[2]] < last) { last = T.cpos[2 * B + l[2]]; ae = 2; }
       R acc, Tr;
-      march<R>(tile, lc, last, T.cev, acc, Tr);
+      march<R>(tile, tc, last, T.cev, acc, Tr);
       const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
       const int row = (ae * 2) * B + l[ae];
       const R Iin = face_value<R>(fin, fstride, B, ae, l[eb], l[ec], T.ck[row], T.ck[row + B], T.cw[row],
@@ -414,8 +424,9 @@ int cell_parts(int B) {
 
 template <typename R, int BC>
 void face_launch(const GridDims &g, const R *kappa, const R *S, const R *Ib, const unsigned char *tpl,
-                 const FaceItem *items, int nitems, R *faces, cudaStream_t st) {
-  face_pass_kernel<R, BC><<<nitems, 256, smem_bytes<R>(g.B, 1), st>>>(g, kappa, S, Ib, tpl, items, faces);
+                 const FaceItem *items, int nitems, int max_dirs, R *faces, cudaStream_t st) {
+  face_pass_kernel<R, BC><<<nitems, kFaceThreads, smem_bytes<R>(g.B, max_dirs), st>>>(g, kappa, S, Ib, tpl, items,
+                                                                                       faces);
 }
 
 template <typename R, int MODE, int BC>
@@ -449,12 +460,12 @@ cudaError_t set_smem_attrs() {
 
 template <typename R>
 cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, const R *Ib,
-                              const unsigned char *tpl, const FaceItem *items, int nitems, R *faces,
+                              const unsigned char *tpl, const FaceItem *items, int nitems, int max_dirs, R *faces,
                               cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  if (g.B == 16) face_launch<R, 16>(g, kappa, S, Ib, tpl, items, nitems, faces, st);
-  else if (g.B == 8) face_launch<R, 8>(g, kappa, S, Ib, tpl, items, nitems, faces, st);
-  else face_launch<R, 0>(g, kappa, S, Ib, tpl, items, nitems, faces, st);
+  if (g.B == 16) face_launch<R, 16>(g, kappa, S, Ib, tpl, items, nitems, max_dirs, faces, st);
+  else if (g.B == 8) face_launch<R, 8>(g, kappa, S, Ib, tpl, items, nitems, max_dirs, faces, st);
+  else face_launch<R, 0>(g, kappa, S, Ib, tpl, items, nitems, max_dirs, faces, st);
   return cudaGetLastError();
 }
 
@@ -497,9 +508,8 @@ cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef,
   return cudaGetLastError();
 }
 
-size_t pass_smem_bytes(int B, int nnode, bool fp64) {
-  (void)nnode;
-  return fp64 ? smem_bytes<double>(B, 1) : smem_bytes<float>(B, 1);
+size_t pass_smem_bytes(int B, int dirs, bool fp64) {
+  return fp64 ? smem_bytes<double>(B, dirs) : smem_bytes<float>(B, dirs);
 }
 
 // Opt the shared-memory-heavy kernels in to the full 227 KB per CTA on the
@@ -512,7 +522,8 @@ cudaError_t prepare_kernels() {
 
 #define VET_INSTANTIATE(R)                                                                                      \
   template cudaError_t launch_face_level<R>(const GridDims &, const R *, const R *, const R *,                \
-                                            const unsigned char *, const FaceItem *, int, R *, cudaStream_t);  \
+                                            const unsigned char *, const FaceItem *, int, int, R *,            \
+                                            cudaStream_t);                                                      \
   template cudaError_t launch_cell_pass<R>(const GridDims &, int, const R *, const R *, const R *,            \
                                            const unsigned char *, const R *, R *, R *, R *, R *, void *,       \
                                            cudaStream_t);                                                       \
