@@ -82,8 +82,10 @@ typedef struct {
 typedef struct {
   int nside;
   double rot_q[4];
-  int precision; /* VET_FP32 or VET_FP64 */
-  int device;    /* CUDA device ordinal the context works on */
+  int precision;        /* VET_FP32 or VET_FP64 */
+  int device;           /* CUDA device ordinal the context works on */
+  long long spin_limit; /* polls per device-side wait before it gives up and
+                           the call reports VET_ETIMEOUT; 0 = default (2^22) */
 } vet_config;
 
 typedef struct vet_ctx vet_ctx;
@@ -125,7 +127,10 @@ vet_status vet_moments_f64(vet_ctx *ctx, const double *I, double *M_out, void *s
 vet_status vet_closure_f64(vet_ctx *ctx, const double *kappa, const double *S, const double *Ib,
                            double *f_out, double *M_out, void *stream);
 
-/* Wait for the context's last enqueued work and report any device error. */
+/* Wait for the context's last enqueued work and report any device error:
+ * VET_ECUDA for a CUDA fault, VET_ETIMEOUT when a bounded device-side wait
+ * (a kernel waiting for its staged data) gave up; the outputs of that call are
+ * then incomplete.  The context stays usable either way. */
 vet_status vet_sync(vet_ctx *ctx);
 
 /* Work measure of one closure, from the ray templates: the number of

@@ -30,10 +30,14 @@ struct vet_ctx {
   std::vector<int> level_off;    // face items of level L: [level_off[L], level_off[L+1])
   void *d_tpl = nullptr;         // N template blobs, internal (octant-sorted) order
   FaceItem *d_items = nullptr;
+  int *d_cell_order = nullptr;   // cell-pass visiting order of internal directions
   void *d_faces = nullptr;       // [N][blocks][3][fstride], upwind frame, padded
   void *d_emax = nullptr;        // 8 bytes: bit pattern of max E (nonnegative)
   void *d_E = nullptr;           // [cells] E when the caller does not want M
   void *d_coef = nullptr;        // [N][10] w (1, n, nn), HEALPix order
+  void *d_bnd = nullptr;         // [6][N][fstride] boundary faces of the current call
+  int *d_status = nullptr;       // device error bits (bounded waits that gave up)
+  long long spin = 0;            // polls per device-side wait
   void *d_stage = nullptr;       // staging of host-pointer arguments
   size_t stage_bytes = 0;
   long long cell_segs = 0, face_segs = 0;
@@ -157,7 +161,9 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   }
   hd->w = R(d[3]);
   hd->ext = ext;
-  const int stride[3] = {1, vet::tile_stride_y(B), vet::tile_stride_z(B)};
+  const vet::TileShape ct = vet::cell_tile(B), nt = vet::node_tile(B);
+  const int cstride[3] = {1, ct.sy, ct.sz};  // cell rays walk the cell-pass tile
+  const int nstride[3] = {1, nt.sy, nt.sz};  // node rays walk the face-pass tile
   // cell rays: planes at t = (m + 1/2)/|n_a|, m = 0..B-1
   std::vector<Event> ev;
   for (int a = 0; a < 3; ++a)
@@ -169,7 +175,7 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   for (size_t e = 0; e < ev.size(); ++e) {
     cpos[ev[e].axis * B + ev[e].m] = (int16_t)e;
     cev[e].len = R((ev[e].t - prev) * scale);
-    cev[e].delta = -sgn[ev[e].axis] * stride[ev[e].axis];
+    cev[e].delta = -sgn[ev[e].axis] * cstride[ev[e].axis];
     prev = ev[e].t;
   }
   // node rays: planes at t = m/|n_a|, m = 1..B
@@ -186,7 +192,7 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   for (size_t e = 0; e < ev.size(); ++e) {
     npos[ev[e].axis * (B + 1) + ev[e].m] = (int16_t)e;
     nev[e].len = R((ev[e].t - prev) * scale);
-    nev[e].delta = -sgn[ev[e].axis] * stride[ev[e].axis];
+    nev[e].delta = -sgn[ev[e].axis] * nstride[ev[e].axis];
     prev = ev[e].t;
   }
   // exit tables: leaving through axis a at depth D, the in-plane upwind-frame
@@ -250,10 +256,13 @@ void free_ctx(vet_ctx *c) {
     if (e) cudaEventDestroy(e);
   cudaFree(c->d_tpl);
   cudaFree(c->d_items);
+  cudaFree(c->d_cell_order);
   cudaFree(c->d_faces);
   cudaFree(c->d_emax);
   cudaFree(c->d_E);
   cudaFree(c->d_coef);
+  cudaFree(c->d_bnd);
+  cudaFree(c->d_status);
   cudaFree(c->d_stage);
   delete c;
 }
@@ -301,6 +310,11 @@ vet_status build_context(vet_ctx *c) {
             per_level[L].push_back({id, d0, std::min(kGroup, ob[o + 1] - d0), 0});
         }
   }
+  // cell-pass order: octants interleaved round robin
+  std::vector<int> cell_order;
+  for (int r = 0; (int)cell_order.size() < N; ++r)
+    for (int o = 0; o < 8; ++o)
+      if (ob[o] + r < ob[o + 1]) cell_order.push_back(ob[o] + r);
   std::vector<FaceItem> items;
   c->level_off.assign(c->nlevels + 1, 0);
   for (int L = 0; L < c->nlevels; ++L) {
@@ -328,11 +342,18 @@ vet_status build_context(vet_ctx *c) {
   if ((e = cudaMalloc(&c->d_emax, 8))) return cuda_err(c, e, "cudaMalloc(emax)");
   if ((e = cudaMalloc(&c->d_E, sizeof(R) * c->dims.ncell))) return cuda_err(c, e, "cudaMalloc(E)");
   if ((e = cudaMalloc(&c->d_coef, sizeof(R) * coef.size()))) return cuda_err(c, e, "cudaMalloc(coef)");
+  if ((e = cudaMalloc(&c->d_bnd, sizeof(R) * 6 * (size_t)N * c->dims.fstride)))
+    return cuda_err(c, e, "cudaMalloc(boundary faces)");
+  if ((e = cudaMalloc((void **)&c->d_status, sizeof(int)))) return cuda_err(c, e, "cudaMalloc(status)");
+  if ((e = cudaMemset(c->d_status, 0, sizeof(int)))) return cuda_err(c, e, "cudaMemset(status)");
   if ((e = cudaMemcpy(c->d_tpl, tpl.data(), tpl.size(), cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload templates");
   if (!items.empty() &&
       (e = cudaMemcpy(c->d_items, items.data(), sizeof(FaceItem) * items.size(), cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload schedule");
+  if ((e = cudaMalloc((void **)&c->d_cell_order, sizeof(int) * N))) return cuda_err(c, e, "cudaMalloc(order)");
+  if ((e = cudaMemcpy(c->d_cell_order, cell_order.data(), sizeof(int) * N, cudaMemcpyHostToDevice)))
+    return cuda_err(c, e, "upload order");
   if ((e = cudaMemcpy(c->d_coef, coef.data(), sizeof(R) * coef.size(), cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload coefficients");
   if ((e = vet::prepare_kernels())) return cuda_err(c, e, "cudaFuncSetAttribute");
@@ -429,6 +450,19 @@ vet_status stage_args(vet_ctx *c, cudaStream_t st, std::vector<std::pair<const R
   return VET_OK;
 }
 
+// Reads and clears the device status word (the stream must be idle).
+vet_status check_status(vet_ctx *c) {
+  int st = 0;
+  cudaError_t e = cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) return cuda_err(c, e, "status read");
+  if (st) {
+    cudaMemset(c->d_status, 0, sizeof(int));
+    return set_err(c, VET_ETIMEOUT,
+                   "a device-side wait gave up (status bits " + std::to_string(st) + "); outputs are incomplete");
+  }
+  return VET_OK;
+}
+
 template <typename R>
 vet_status finish_args(vet_ctx *c, cudaStream_t st, const std::vector<std::pair<R *, R *>> &copy_back,
                        const std::vector<size_t> &bytes, bool had_host) {
@@ -439,6 +473,7 @@ vet_status finish_args(vet_ctx *c, cudaStream_t st, const std::vector<std::pair<
   if (had_host) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e) return cuda_err(c, e, "stream synchronize");
+    return check_status(c);
   }
   return VET_OK;
 }
@@ -454,11 +489,12 @@ vet_status mark(vet_ctx *c, int i, cudaStream_t st) {
 
 template <typename R>
 vet_status run_face_pass(vet_ctx *c, const R *kappa, const R *S, const R *Ib, cudaStream_t st) {
+  cudaError_t e = vet::launch_fill_boundary<R>(c->dims, (const unsigned char *)c->d_tpl, Ib, (R *)c->d_bnd, st);
+  if (e) return cuda_err(c, e, "boundary fill launch");
   for (int L = 0; L < c->nlevels; ++L) {
     const int n = c->level_off[L + 1] - c->level_off[L];
-    cudaError_t e = vet::launch_face_level<R>(c->dims, kappa, S, Ib, (const unsigned char *)c->d_tpl,
-                                               c->d_items + c->level_off[L], n, vet::kFaceGroup, (R *)c->d_faces,
-                                               st);
+    e = vet::launch_face_level<R>(c->dims, kappa, S, (const unsigned char *)c->d_tpl, c->d_items + c->level_off[L], n,
+                                  vet::kFaceGroup, (R *)c->d_faces, (const R *)c->d_bnd, c->spin, c->d_status, st);
     if (e) return cuda_err(c, e, "face pass launch");
   }
   return VET_OK;
@@ -485,8 +521,9 @@ vet_status do_trace(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *I_ou
   if ((s = mark(c, 0, st))) return s;
   if ((s = run_face_pass<R>(c, din[0], din[1], din[2], st))) return s;
   if ((s = mark(c, 1, st))) return s;
-  cudaError_t e = vet::launch_cell_pass<R>(c->dims, 1, din[0], din[1], din[2], (const unsigned char *)c->d_tpl,
-                                           (const R *)c->d_faces, dout[0], nullptr, nullptr, nullptr, nullptr, st);
+  cudaError_t e = vet::launch_cell_pass<R>(c->dims, 1, din[0], din[1], (const unsigned char *)c->d_tpl,
+                                           c->d_cell_order, (const R *)c->d_faces, (const R *)c->d_bnd, dout[0],
+                                           nullptr, nullptr, nullptr, nullptr, c->spin, c->d_status, st);
   if (e) return cuda_err(c, e, "cell pass launch");
   if ((s = mark(c, 2, st)) || (s = mark(c, 3, st))) return s;
   c->last_stream = st;
@@ -540,8 +577,9 @@ vet_status do_closure(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *f_
   if ((s = run_face_pass<R>(c, din[0], din[1], din[2], st))) return s;
   if ((s = mark(c, 1, st))) return s;
   R *Mdev = dout[1];
-  e = vet::launch_cell_pass<R>(c->dims, 0, din[0], din[1], din[2], (const unsigned char *)c->d_tpl,
-                               (const R *)c->d_faces, nullptr, Mdev, (R *)c->d_E, dout[0], c->d_emax, st);
+  e = vet::launch_cell_pass<R>(c->dims, 0, din[0], din[1], (const unsigned char *)c->d_tpl, c->d_cell_order,
+                               (const R *)c->d_faces, (const R *)c->d_bnd, nullptr, Mdev, (R *)c->d_E, dout[0],
+                               c->d_emax, c->spin, c->d_status, st);
   if (e) return cuda_err(c, e, "cell pass launch");
   if ((s = mark(c, 2, st))) return s;
   const R *E = Mdev ? Mdev : (const R *)c->d_E;
@@ -572,7 +610,7 @@ VET_API vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_con
   if (!(qn > 1e-12) || !std::isfinite(qn)) return set_err(nullptr, VET_EINVAL, "rotation quaternion is zero or not finite");
   const bool fp64 = cfg->precision == VET_FP64;
   const int nnode = (g.block + 1) * (g.block + 1);
-  if (vet::pass_smem_bytes(g.block, vet::kFaceGroup, fp64) > 232448)
+  if (vet::pass_smem_bytes(g.block, vet::kFaceGroup, fp64) > 232448 - 64)
     return set_err(nullptr, VET_EUNSUPPORTED, "block edge too large for one CTA's shared memory at this precision");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -584,6 +622,7 @@ VET_API vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_con
   if (!c) return set_err(nullptr, VET_ENOMEM, "host allocation failed");
   c->grid = g;
   c->cfg = *cfg;
+  c->spin = cfg->spin_limit > 0 ? cfg->spin_limit : (1LL << 22);
   c->fp64 = fp64;
   c->N = 12 * cfg->nside * cfg->nside;
   c->dims.nx = g.nx;
@@ -665,7 +704,7 @@ VET_API vet_status vet_sync(vet_ctx *ctx) {
   cudaError_t e = cudaStreamSynchronize(ctx->last_stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e) return cuda_err(ctx, e, "device work failed");
-  return VET_OK;
+  return check_status(ctx);
 }
 
 VET_API vet_status vet_work_counts(const vet_ctx *ctx, long long *cell_segments, long long *face_segments) {

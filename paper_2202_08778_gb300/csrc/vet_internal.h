@@ -91,13 +91,17 @@ struct GridDims {
   long long ncell;    // nx*ny*nz
 };
 
-// Shared-memory kappa/S tile of a block: cell (x, y, z) at
-// x + (B+1) y + (B+1)^2 z.  All three strides are odd, so any uniform shift of
-// a warp's 8-byte accesses along a row, column or pillar of the block is free
-// of bank conflicts.
-__host__ __device__ inline int tile_stride_y(int B) { return B + 1; }
-__host__ __device__ inline int tile_stride_z(int B) { return (B + 1) * (B + 1); }
-__host__ __device__ inline int tile_elems(int B) { return (B + 1) * (B + 1) * B; }
+// Shared-memory kappa/S tiles of a block.  Face pass: cell (x, y, z) at
+// x + (B+1) y + (B+1)^2 z; the three strides are odd, so a warp walking a row,
+// column or pillar of a face (and any uniform shift of it) touches distinct
+// banks with its 8-byte loads.  Cell pass: x + (B+4) y + (B+4) B z; with B a
+// multiple of 8 the y stride is 4 or 12 mod 16, so a 4 x 4 layer of a warp's
+// 4 x 4 x 2 cell brick is conflict free.
+struct TileShape {
+  int sy, sz, elems;
+};
+__host__ __device__ inline TileShape node_tile(int B) { return {B + 1, (B + 1) * (B + 1), (B + 1) * (B + 1) * B}; }
+__host__ __device__ inline TileShape cell_tile(int B) { return {B + 4, (B + 4) * B, (B + 4) * B * B}; }
 
 // Stored faces: node (ub, uc) of a face, in the upwind frame of the direction
 // (the in-plane axes flipped where the direction component is negative), at
@@ -118,19 +122,30 @@ struct FaceItem {
 };
 
 // Launchers (vet_kernels.cu).  All return the cudaGetLastError() of the
-// launch.  R = float or double.
+// launch.  R = float or double.  `bnd` holds the boundary faces materialised
+// by launch_fill_boundary; `spin` bounds every device-side wait (polls of an
+// mbarrier); a wait that gives up ORs a code into *status and the kernel
+// returns early with its outputs incomplete.
+//   status bits: 1 face-pass staging, 2 cell-pass staging, 4 cell-pass buffer
+//   release.
+
 // Face pass of one wavefront level: nitems items of at most max_dirs
 // directions each.
 template <typename R>
-cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, const R *Ib,
-                              const unsigned char *tpl, const FaceItem *items, int nitems, int max_dirs, R *faces,
-                              cudaStream_t st);
+cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, const unsigned char *tpl,
+                              const FaceItem *items, int nitems, int max_dirs, R *faces, const R *bnd,
+                              long long spin, int *status, cudaStream_t st);
 
-// mode 0: moments + f (+ E for the floor rule); mode 1: write I_out.
+// mode 0: moments + f (+ E for the floor rule); mode 1: write I_out.  The
+// directions are visited in cell_order.
 template <typename R>
-cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const R *Ib,
-                             const unsigned char *tpl, const R *faces, R *I_out, R *M_out, R *E_out,
-                             R *f_out, void *emax_bits, cudaStream_t st);
+cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const unsigned char *tpl,
+                             const int *cell_order, const R *faces, const R *bnd, R *I_out, R *M_out, R *E_out,
+                             R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st);
+
+// bnd[face][d] <- constant Ib[face][ext(d)] (or 0 when Ib is NULL).
+template <typename R>
+cudaError_t launch_fill_boundary(const GridDims &g, const unsigned char *tpl, const R *Ib, R *bnd, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_floor_fix(long long ncell, const R *E, long long E_stride, const void *emax_bits,
@@ -142,6 +157,9 @@ cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef,
 
 // Dynamic shared memory of a CTA staging `dirs` directions.
 size_t pass_smem_bytes(int B, int dirs, bool fp64);
+
+// Bytes of one staged direction (template + three faces).
+size_t face_slot_bytes(int B, bool fp64);
 
 // Directions per face-pass item.
 constexpr int kFaceGroup = 4;

@@ -122,108 +122,165 @@ __device__ __forceinline__ R face_value(const R *__restrict__ fin, int fstride, 
   return wb.y * (wc.y * F[0] + wc.x * F[1]) + wb.x * (wc.y * F[W] + wc.x * F[W + 1]);
 }
 
-// Copy `bytes` (a multiple of 16) with the whole CTA.
-__device__ __forceinline__ void cta_copy16(void *dst, const void *src, int bytes) {
-  const int4 *s = reinterpret_cast<const int4 *>(src);
-  int4 *d = reinterpret_cast<int4 *>(dst);
-  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = s[i];
+// ------------------------------------------------ TMA bulk copies + mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// The three faces entering block (bx, by, bz) for internal direction d: the
-// upwind neighbours' stored downwind faces, or the constant boundary value.
+// Make barrier initialisation visible to the async (TMA) proxy.
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Producer arrival that also announces `bytes` of incoming bulk copies.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the completion of phase `parity`: gives up after
+// `limit` polls, records `code` in the device status word and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit, int *status, int code) {
+  const uint32_t a = smem_u32(bar);
+  for (long long i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  atomicOr(status, code);
+  return false;
+}
+
+// One bulk copy global -> shared (16-byte aligned addresses and size),
+// completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// A staged direction ("slot") in shared memory: its template blob followed
+// by its three incoming faces.  Called by one thread: issues the four bulk
+// copies of internal direction d for block (bx, by, bz); the faces come from
+// the upwind neighbours' stored downwind faces or from the materialised
+// boundary faces bnd[face][d].
 template <typename R>
-__device__ __forceinline__ void stage_incoming(R *fin, const GridDims &g, int bx, int by, int bz, int d,
-                                               const TplHead<R> *__restrict__ hd, const R *__restrict__ faces,
-                                               const R *__restrict__ Ib) {
+__device__ __forceinline__ void issue_slot(unsigned char *slot, const GridDims &g, const TplLayout &TL, int bx,
+                                           int by, int bz, int d, const unsigned char *__restrict__ tpl_g,
+                                           const R *__restrict__ faces, const R *__restrict__ bnd, uint64_t *bar) {
+  const unsigned char *src = tpl_g + (size_t)d * TL.bytes;
+  bulk_g2s(slot, src, (uint32_t)TL.bytes, bar);
+  const TplHead<R> *hd = reinterpret_cast<const TplHead<R> *>(src);
   const int nblk = g.nbx * g.nby * g.nbz;
+  const uint32_t fb = (uint32_t)(g.fstride * sizeof(R));
   const int b3[3] = {bx, by, bz};
   const int nb3[3] = {g.nbx, g.nby, g.nbz};
   for (int a = 0; a < 3; ++a) {
     const int s = hd->sgn[a];
     int nb[3] = {b3[0], b3[1], b3[2]};
     nb[a] -= s;
-    R *dst = fin + a * g.fstride;
+    const R *fsrc;
     if (nb[a] < 0 || nb[a] >= nb3[a]) {
       const int face = 2 * a + (s > 0 ? 0 : 1);
-      const R v = Ib ? Ib[(long long)face * g.ndir + hd->ext] : R(0);
-      for (int i = threadIdx.x; i < g.fstride; i += blockDim.x) dst[i] = v;
+      fsrc = bnd + ((long long)face * g.ndir + d) * g.fstride;
     } else {
       const long long nid = ((long long)nb[2] * g.nby + nb[1]) * g.nbx + nb[0];
-      cta_copy16(dst, faces + (((long long)d * nblk + nid) * 3 + a) * g.fstride, g.fstride * (int)sizeof(R));
+      fsrc = faces + (((long long)d * nblk + nid) * 3 + a) * g.fstride;
     }
+    bulk_g2s(slot + TL.bytes + a * fb, fsrc, fb, bar);
   }
 }
 
+template <typename R>
+__host__ __device__ inline size_t slot_bytes(int B) {
+  return (size_t)tpl_layout<R>(B).bytes + sizeof(R) * 3 * (size_t)face_stride_elems<R>(B);
+}
+
 template <typename R, int BC>
-__device__ __forceinline__ void load_tile(vec2_t<R> *tile, const GridDims &g, int bx, int by, int bz,
+__device__ __forceinline__ void load_tile(vec2_t<R> *tile, TileShape ts, const GridDims &g, int bx, int by, int bz,
                                           const R *__restrict__ kappa, const R *__restrict__ S) {
   const int B = BC ? BC : g.B;
   const int B2 = B * B, B3 = B2 * B;
-  const int TY = tile_stride_y(B), TZ = tile_stride_z(B);
   for (int i = threadIdx.x; i < B3; i += blockDim.x) {
     const int x = i % B, y = (i / B) % B, z = i / B2;
     const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
     vec2_t<R> v;
     v.x = kappa[gi];
     v.y = S[gi];
-    tile[x + TY * y + TZ * z] = v;
+    tile[x + ts.sy * y + ts.sz * z] = v;
   }
 }
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Dynamic shared memory of a CTA that stages `dt` directions at a time.
+// Dynamic shared memory of a CTA holding `nslots` staged directions.
 template <typename R>
-__host__ __device__ inline size_t smem_bytes(int B, int dt) {
-  return align16(sizeof(vec2_t<R>) * (size_t)tile_elems(B)) +
-         (size_t)dt * (sizeof(R) * 3 * (size_t)face_stride_elems<R>(B) + (size_t)tpl_layout<R>(B).bytes);
+__host__ __device__ inline size_t smem_bytes(int B, int nslots) {
+  const int te = node_tile(B).elems > cell_tile(B).elems ? node_tile(B).elems : cell_tile(B).elems;
+  return align16(sizeof(vec2_t<R>) * (size_t)te) + (size_t)nslots * slot_bytes<R>(B);
 }
 
-constexpr int kDirTile = 8;   // directions staged per cell-pass tile
-constexpr size_t kSmemMax = 232448;
+constexpr int kDirTile = 4;   // directions per cell-pass tile (two tiles in flight)
+constexpr size_t kSmemMax = 232448 - 64;  // opt-in limit less the static mbarriers
 
 template <typename R>
 int cell_dir_tile(int B) {
   int dt = kDirTile;
-  while (dt > 1 && smem_bytes<R>(B, dt) > kSmemMax) --dt;
+  while (dt > 1 && smem_bytes<R>(B, 2 * dt) > kSmemMax) --dt;
   return dt;
 }
 
 // ---------------------------------------------------------------- face pass
 constexpr int kFaceThreads = 512;
 
-// Face pass: one CTA per item (a block and up to `dt` directions of one
-// octant at the same wavefront level).  The item's templates and incoming
-// faces are staged at once, then the (direction, node) rays are spread over
-// the CTA's threads.
+// Face pass: one CTA per item (a block and up to kFaceGroup directions of one
+// octant at the same wavefront level).  One thread issues the TMA bulk copies
+// of the item's templates and incoming faces, all in flight at once, while
+// the CTA loads the block's kappa/S tile; then the (direction, node) rays are
+// spread over the threads.
 template <typename R, int BC>
 __global__ void __launch_bounds__(kFaceThreads, 2)
-    face_pass_kernel(GridDims g, const R *__restrict__ kappa, const R *__restrict__ S, const R *__restrict__ Ib,
+    face_pass_kernel(GridDims g, const R *__restrict__ kappa, const R *__restrict__ S,
                      const unsigned char *__restrict__ tpl_g, const FaceItem *__restrict__ items,
-                     R *__restrict__ faces) {
+                     R *__restrict__ faces, const R *__restrict__ bnd, long long spin_limit, int *status) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full;
   const int B = BC ? BC : g.B;
   const int W = B + 2, N1 = B + 1, NN = N1 * N1, NN3 = 3 * NN;
-  const int TY = tile_stride_y(B), TZ = tile_stride_z(B);
+  const TileShape ts = node_tile(B);
   const TplLayout TL = tpl_layout<R>(B);
-  const size_t fbytes = sizeof(R) * 3 * (size_t)g.fstride;
+  const size_t sb = slot_bytes<R>(B);
   const FaceItem it = items[blockIdx.x];
   vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
-  unsigned char *fin_base = smem + align16(sizeof(vec2_t<R>) * (size_t)tile_elems(B));
-  unsigned char *tb_base = fin_base + fbytes * it.dir_count;
+  unsigned char *slots = smem + align16(sizeof(vec2_t<R>) * (size_t)ts.elems);
   const int bx = it.block % g.nbx, by = (it.block / g.nbx) % g.nby, bz = it.block / (g.nbx * g.nby);
   const int nblk = g.nbx * g.nby * g.nbz;
-  load_tile<R, BC>(tile, g, bx, by, bz, kappa, S);
-  cta_copy16(tb_base, tpl_g + (size_t)it.dir_begin * TL.bytes, it.dir_count * TL.bytes);
-  for (int j = 0; j < it.dir_count; ++j)
-    stage_incoming<R>(reinterpret_cast<R *>(fin_base + fbytes * j), g, bx, by, bz, it.dir_begin + j,
-                      reinterpret_cast<const TplHead<R> *>(tpl_g + (size_t)(it.dir_begin + j) * TL.bytes), faces,
-                      Ib);
+  if (threadIdx.x == 0) {
+    mbar_init(&full, 1);
+    mbar_fence_init();
+    mbar_expect_tx(&full, (uint32_t)(sb * it.dir_count));
+    for (int j = 0; j < it.dir_count; ++j)
+      issue_slot<R>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full);
+  }
+  load_tile<R, BC>(tile, ts, g, bx, by, bz, kappa, S);
   __syncthreads();
+  if (!mbar_wait(&full, 0, spin_limit, status, 1)) return;
   for (int w = threadIdx.x; w < it.dir_count * NN3; w += blockDim.x) {
     const int j = w / NN3, n = w - j * NN3;
-    const Tpl<R> T(tb_base + (size_t)j * TL.bytes, TL);
-    const R *fin = reinterpret_cast<const R *>(fin_base + fbytes * j);
+    const Tpl<R> T(slots + sb * j, TL);
+    const R *fin = reinterpret_cast<const R *>(slots + sb * j + TL.bytes);
     const int a = n / NN, r = n - a * NN;
     const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
     const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
@@ -238,7 +295,7 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     if (last >= 0) {  // then every L >= 1 and the start cell is inside the block
       int cell[3];
       for (int q = 0; q < 3; ++q) cell[q] = T.h->sgn[q] > 0 ? L[q] - 1 : B - L[q];
-      march<R>(tile, cell[0] + TY * cell[1] + TZ * cell[2], last, T.nev, acc, Tr);
+      march<R>(tile, cell[0] + ts.sy * cell[1] + ts.sz * cell[2], last, T.nev, acc, Tr);
     }
     const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
     const int row = (ae * 2) * N1 + L[ae];
@@ -259,34 +316,69 @@ __device__ __forceinline__ void atomic_max_nonneg(void *p, double v) {
 
 constexpr int kCellThreads = 512;  // one cell per thread
 
-// Cell pass: one CTA per (block, slab of up to 512 of the block's cells), one
-// cell per thread; all directions are visited in tiles of `dt` (templates and
-// incoming faces of a whole tile are staged at once, so warps synchronise once
-// per tile, not per direction).
+// Cell pass: one CTA per (block, slab of 512 of the block's cells), one cell
+// per thread.  Directions are visited in tiles of `dt` (octants interleaved)
+// through two shared-memory buffers: thread 0 issues the TMA bulk copies of
+// tile t + 2 as soon as every warp has released the buffer of tile t, so the
+// loads run behind the ray work; warps wait only on the "full" barrier of the
+// tile they start.  For block edges that are multiples of 4, each warp holds a
+// 4 x 4 x 2 brick of cells, whose rays have similar lengths.
 template <typename R, int MODE, int BC>
 __global__ void __launch_bounds__(kCellThreads, 2)
     cell_pass_kernel(GridDims g, int parts, int dt, const R *__restrict__ kappa, const R *__restrict__ S,
-                     const R *__restrict__ Ib, const unsigned char *__restrict__ tpl_g, const R *__restrict__ faces,
-                     R *__restrict__ I_out, R *__restrict__ M_out, R *__restrict__ E_out, R *__restrict__ f_out,
-                     void *emax_bits) {
+                     const unsigned char *__restrict__ tpl_g, const int *__restrict__ order,
+                     const R *__restrict__ faces, const R *__restrict__ bnd, R *__restrict__ I_out,
+                     R *__restrict__ M_out, R *__restrict__ E_out, R *__restrict__ f_out, void *emax_bits,
+                     long long spin_limit, int *status) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[2], empty[2];
   const int B = BC ? BC : g.B;
   const int B2 = B * B, B3 = B2 * B;
+  const TileShape ts = cell_tile(B);
   const TplLayout TL = tpl_layout<R>(B);
   const int fstride = g.fstride;
-  const size_t fbytes = sizeof(R) * 3 * (size_t)fstride;
+  const size_t sb = slot_bytes<R>(B);
   vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
-  unsigned char *fin_base = smem + align16(sizeof(vec2_t<R>) * (size_t)tile_elems(B));
-  unsigned char *tb_base = fin_base + fbytes * dt;
+  unsigned char *buf0 = smem + align16(sizeof(vec2_t<R>) * (size_t)ts.elems);
   const int blk = blockIdx.x / parts, part = blockIdx.x - blk * parts;
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
   const int cpc = B3 / parts;  // cells of this CTA
-  load_tile<R, BC>(tile, g, bx, by, bz, kappa, S);
+  const int nwarps = blockDim.x >> 5;
+  const int ntiles = (g.ndir + dt - 1) / dt;
+  auto issue_tile = [&](int t) {  // thread 0 only
+    const int b = t & 1, d0 = t * dt, nd = min(dt, g.ndir - d0);
+    unsigned char *buf = buf0 + (size_t)b * dt * sb;
+    mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
+    for (int j = 0; j < nd; ++j) issue_slot<R>(buf + sb * j, g, TL, bx, by, bz, order[d0 + j], tpl_g, faces, bnd, &full[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], nwarps);
+    mbar_init(&empty[1], nwarps);
+    mbar_fence_init();
+    issue_tile(0);
+    if (ntiles > 1) issue_tile(1);
+  }
+  load_tile<R, BC>(tile, ts, g, bx, by, bz, kappa, S);
+  __syncthreads();
 
   const bool active = (int)threadIdx.x < cpc;
-  const int lc = part * cpc + (active ? (int)threadIdx.x : 0);  // local cell index in the block
-  const int cx = lc % B, cy = (lc / B) % B, cz = lc / B2;
-  const int tc = cx + tile_stride_y(B) * cy + tile_stride_z(B) * cz;  // tile index
+  int cx, cy, cz;
+  if (BC != 0 && BC % 4 == 0 && cpc == kCellThreads) {
+    // slab of B x B x (512 / B^2) cells; warp w holds brick w of 4 x 4 x 2
+    const int nbx4 = B / 4;
+    const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    cx = 4 * (w % nbx4) + (ln & 3);
+    cy = 4 * ((w / nbx4) % nbx4) + ((ln >> 2) & 3);
+    cz = 2 * (w / (nbx4 * nbx4)) + (ln >> 4) + part * (kCellThreads / B2);
+  } else {
+    const int lc = part * cpc + (active ? (int)threadIdx.x : 0);
+    cx = lc % B;
+    cy = (lc / B) % B;
+    cz = lc / B2;
+  }
+  const int tc = cx + ts.sy * cy + ts.sz * cz;  // tile index
   const long long gc = ((long long)(bz * B + cz) * g.ny + (by * B + cy)) * g.nx + (bx * B + cx);
   // Moments accumulated over all directions.  E, Pxx, Pyy and Pzz (sums of
   // positive terms that f_ii = P_ii / E depends on) carry a Kahan
@@ -296,58 +388,64 @@ __global__ void __launch_bounds__(kCellThreads, 2)
   for (int m = 0; m < 10; ++m) mom[m] = R(0);
   for (int m = 0; m < 4; ++m) cmp[m] = R(0);
 
-  for (int d0 = 0; d0 < g.ndir; d0 += dt) {
-    const int nd = min(dt, g.ndir - d0);
-    __syncthreads();
-    cta_copy16(tb_base, tpl_g + (size_t)d0 * TL.bytes, nd * TL.bytes);
-    for (int j = 0; j < nd; ++j)
-      stage_incoming<R>(reinterpret_cast<R *>(fin_base + fbytes * j), g, bx, by, bz, d0 + j,
-                        reinterpret_cast<const TplHead<R> *>(tpl_g + (size_t)(d0 + j) * TL.bytes), faces, Ib);
-    __syncthreads();
-    if (!active) continue;
-    for (int j = 0; j < nd; ++j) {
-      const Tpl<R> T(tb_base + (size_t)j * TL.bytes, TL);
-      const R *fin = reinterpret_cast<const R *>(fin_base + fbytes * j);
-      int l[3];
-      l[0] = T.h->sgn[0] > 0 ? cx : B - 1 - cx;
-      l[1] = T.h->sgn[1] > 0 ? cy : B - 1 - cy;
-      l[2] = T.h->sgn[2] > 0 ? cz : B - 1 - cz;
-      int last = T.cpos[l[0]], ae = 0;
-      if (T.cpos[B + l[1]] < last) { last = T.cpos[B + l[1]]; ae = 1; }
-      if (T.cpos[2 * B + l[2]] < last) { last = T.cpos[2 * B + l[2]]; ae = 2; }
-      R acc, Tr;
-      march<R>(tile, tc, last, T.cev, acc, Tr);
-      const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
-      const int row = (ae * 2) * B + l[ae];
-      const R Iin = face_value<R>(fin, fstride, B, ae, l[eb], l[ec], T.ck[row], T.ck[row + B], T.cw[row],
-                                  T.cw[row + B]);
-      const R I = fma(Tr, Iin, acc);
-      if (MODE == 1) {
-        I_out[(long long)T.h->ext * g.ncell + gc] = I;
-      } else {
-        const R w = T.h->w, nx = T.h->n[0], ny = T.h->n[1], nz = T.h->n[2];
-        const R wI = w * I, wIx = wI * nx, wIy = wI * ny, wIz = wI * nz;
-        const R term[4] = {wI, wIx * nx, wIy * ny, wIz * nz};
+  bool ok = true;
+  for (int t = 0; t < ntiles && ok; ++t) {
+    const int b = t & 1;
+    const uint32_t ph = (uint32_t)((t >> 1) & 1);
+    if (!mbar_wait(&full[b], ph, spin_limit, status, 2)) { ok = false; break; }
+    const int nd = min(dt, g.ndir - t * dt);
+    const unsigned char *buf = buf0 + (size_t)b * dt * sb;
+    if (active) {
+      for (int j = 0; j < nd; ++j) {
+        const Tpl<R> T(buf + sb * j, TL);
+        const R *fin = reinterpret_cast<const R *>(buf + sb * j + TL.bytes);
+        int l[3];
+        l[0] = T.h->sgn[0] > 0 ? cx : B - 1 - cx;
+        l[1] = T.h->sgn[1] > 0 ? cy : B - 1 - cy;
+        l[2] = T.h->sgn[2] > 0 ? cz : B - 1 - cz;
+        int last = T.cpos[l[0]], ae = 0;
+        if (T.cpos[B + l[1]] < last) { last = T.cpos[B + l[1]]; ae = 1; }
+        if (T.cpos[2 * B + l[2]] < last) { last = T.cpos[2 * B + l[2]]; ae = 2; }
+        R acc, Tr;
+        march<R>(tile, tc, last, T.cev, acc, Tr);
+        const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
+        const int row = (ae * 2) * B + l[ae];
+        const R Iin = face_value<R>(fin, fstride, B, ae, l[eb], l[ec], T.ck[row], T.ck[row + B], T.cw[row],
+                                    T.cw[row + B]);
+        const R I = fma(Tr, Iin, acc);
+        if (MODE == 1) {
+          I_out[(long long)T.h->ext * g.ncell + gc] = I;
+        } else {
+          const R w = T.h->w, nx = T.h->n[0], ny = T.h->n[1], nz = T.h->n[2];
+          const R wI = w * I, wIx = wI * nx, wIy = wI * ny, wIz = wI * nz;
+          const R term[4] = {wI, wIx * nx, wIy * ny, wIz * nz};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {  // E, Pxx, Pyy, Pzz: compensated
-          const int m = q == 0 ? 0 : 3 + q;
-          const R y = term[q] - cmp[q];
-          const R t = mom[m] + y;
-          cmp[q] = (t - mom[m]) - y;
-          mom[m] = t;
+          for (int q = 0; q < 4; ++q) {  // E, Pxx, Pyy, Pzz: compensated
+            const int m = q == 0 ? 0 : 3 + q;
+            const R y = term[q] - cmp[q];
+            const R tt = mom[m] + y;
+            cmp[q] = (tt - mom[m]) - y;
+            mom[m] = tt;
+          }
+          mom[1] += wIx;
+          mom[2] += wIy;
+          mom[3] += wIz;
+          mom[7] = fma(wIx, ny, mom[7]);
+          mom[8] = fma(wIx, nz, mom[8]);
+          mom[9] = fma(wIy, nz, mom[9]);
         }
-        mom[1] += wIx;
-        mom[2] += wIy;
-        mom[3] += wIz;
-        mom[7] = fma(wIx, ny, mom[7]);
-        mom[8] = fma(wIx, nz, mom[8]);
-        mom[9] = fma(wIy, nz, mom[9]);
       }
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[b]);
+    if (threadIdx.x == 0 && t + 2 < ntiles) {
+      if (!mbar_wait(&empty[b], ph, spin_limit, status, 4)) { ok = false; break; }
+      issue_tile(t + 2);
     }
   }
   if (MODE == 0) {
     R emax = R(0);
-    if (active) {
+    if (active && ok) {
       const R E = mom[0];
       if (M_out) {
         for (int m = 0; m < 10; ++m) M_out[m * g.ncell + gc] = mom[m];
@@ -368,6 +466,18 @@ __global__ void __launch_bounds__(kCellThreads, 2)
     }
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(emax_bits, emax);
   }
+}
+
+// Boundary faces of every direction, materialised so that staging is a
+// plain bulk copy: bnd[face][d][i] = Ib[face][ext(d)] (0 for vacuum).
+template <typename R>
+__global__ void fill_boundary_kernel(const GridDims g, const unsigned char *__restrict__ tpl_g, int tpl_bytes,
+                                     const R *__restrict__ Ib, R *__restrict__ bnd) {
+  const int face = blockIdx.y, d = blockIdx.x;
+  const int ext = reinterpret_cast<const TplHead<R> *>(tpl_g + (size_t)d * tpl_bytes)->ext;
+  const R v = Ib ? Ib[(long long)face * g.ndir + ext] : R(0);
+  R *dst = bnd + ((long long)face * g.ndir + d) * g.fstride;
+  for (int i = threadIdx.x; i < g.fstride; i += blockDim.x) dst[i] = v;
 }
 
 template <typename R> __device__ __forceinline__ R load_max(const void *p);
@@ -423,22 +533,23 @@ int cell_parts(int B) {
 }
 
 template <typename R, int BC>
-void face_launch(const GridDims &g, const R *kappa, const R *S, const R *Ib, const unsigned char *tpl,
-                 const FaceItem *items, int nitems, int max_dirs, R *faces, cudaStream_t st) {
-  face_pass_kernel<R, BC><<<nitems, kFaceThreads, smem_bytes<R>(g.B, max_dirs), st>>>(g, kappa, S, Ib, tpl, items,
-                                                                                       faces);
+void face_launch(const GridDims &g, const R *kappa, const R *S, const unsigned char *tpl, const FaceItem *items,
+                 int nitems, int max_dirs, R *faces, const R *bnd, long long spin, int *status, cudaStream_t st) {
+  face_pass_kernel<R, BC><<<nitems, kFaceThreads, smem_bytes<R>(g.B, max_dirs), st>>>(g, kappa, S, tpl, items, faces,
+                                                                                      bnd, spin, status);
 }
 
 template <typename R, int MODE, int BC>
-void cell_launch(const GridDims &g, const R *kappa, const R *S, const R *Ib, const unsigned char *tpl,
-                 const R *faces, R *I_out, R *M_out, R *E_out, R *f_out, void *emax_bits, cudaStream_t st) {
+void cell_launch(const GridDims &g, const R *kappa, const R *S, const unsigned char *tpl, const int *order,
+                 const R *faces, const R *bnd, R *I_out, R *M_out, R *E_out, R *f_out, void *emax_bits,
+                 long long spin, int *status, cudaStream_t st) {
   const int parts = cell_parts(g.B);
   const int cpc = g.B * g.B * g.B / parts;
   const int threads = (cpc + 31) / 32 * 32;
   const int nblk = g.nbx * g.nby * g.nbz;
   const int dt = cell_dir_tile<R>(g.B);
-  cell_pass_kernel<R, MODE, BC><<<nblk * parts, threads, smem_bytes<R>(g.B, dt), st>>>(
-      g, parts, dt, kappa, S, Ib, tpl, faces, I_out, M_out, E_out, f_out, emax_bits);
+  cell_pass_kernel<R, MODE, BC><<<nblk * parts, threads, smem_bytes<R>(g.B, 2 * dt), st>>>(
+      g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, status);
 }
 
 template <typename R>
@@ -459,22 +570,23 @@ cudaError_t set_smem_attrs() {
 }  // namespace
 
 template <typename R>
-cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, const R *Ib,
-                              const unsigned char *tpl, const FaceItem *items, int nitems, int max_dirs, R *faces,
-                              cudaStream_t st) {
+cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, const unsigned char *tpl,
+                              const FaceItem *items, int nitems, int max_dirs, R *faces, const R *bnd,
+                              long long spin, int *status, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  if (g.B == 16) face_launch<R, 16>(g, kappa, S, Ib, tpl, items, nitems, max_dirs, faces, st);
-  else if (g.B == 8) face_launch<R, 8>(g, kappa, S, Ib, tpl, items, nitems, max_dirs, faces, st);
-  else face_launch<R, 0>(g, kappa, S, Ib, tpl, items, nitems, max_dirs, faces, st);
+  if (g.B == 16) face_launch<R, 16>(g, kappa, S, tpl, items, nitems, max_dirs, faces, bnd, spin, status, st);
+  else if (g.B == 8) face_launch<R, 8>(g, kappa, S, tpl, items, nitems, max_dirs, faces, bnd, spin, status, st);
+  else face_launch<R, 0>(g, kappa, S, tpl, items, nitems, max_dirs, faces, bnd, spin, status, st);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const R *Ib,
-                             const unsigned char *tpl, const R *faces, R *I_out, R *M_out, R *E_out,
-                             R *f_out, void *emax_bits, cudaStream_t st) {
-#define VET_CELL(MODE, BC) \
-  cell_launch<R, MODE, BC>(g, kappa, S, Ib, tpl, faces, I_out, M_out, E_out, f_out, emax_bits, st)
+cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const unsigned char *tpl,
+                             const int *order, const R *faces, const R *bnd, R *I_out, R *M_out, R *E_out,
+                             R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st) {
+#define VET_CELL(MODE, BC)                                                                                  \
+  cell_launch<R, MODE, BC>(g, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, \
+                           status, st)
   if (mode == 0) {
     if (g.B == 16) VET_CELL(0, 16);
     else if (g.B == 8) VET_CELL(0, 8);
@@ -485,6 +597,12 @@ cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const 
     else VET_CELL(1, 0);
   }
 #undef VET_CELL
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fill_boundary(const GridDims &g, const unsigned char *tpl, const R *Ib, R *bnd, cudaStream_t st) {
+  fill_boundary_kernel<R><<<dim3(g.ndir, 6), 128, 0, st>>>(g, tpl, tpl_layout<R>(g.B).bytes, Ib, bnd);
   return cudaGetLastError();
 }
 
@@ -512,6 +630,8 @@ size_t pass_smem_bytes(int B, int dirs, bool fp64) {
   return fp64 ? smem_bytes<double>(B, dirs) : smem_bytes<float>(B, dirs);
 }
 
+size_t face_slot_bytes(int B, bool fp64) { return fp64 ? slot_bytes<double>(B) : slot_bytes<float>(B); }
+
 // Opt the shared-memory-heavy kernels in to the full 227 KB per CTA on the
 // current device (the attribute is per device and function).
 cudaError_t prepare_kernels() {
@@ -520,15 +640,17 @@ cudaError_t prepare_kernels() {
   return set_smem_attrs<double>();
 }
 
-#define VET_INSTANTIATE(R)                                                                                      \
-  template cudaError_t launch_face_level<R>(const GridDims &, const R *, const R *, const R *,                \
-                                            const unsigned char *, const FaceItem *, int, int, R *,            \
-                                            cudaStream_t);                                                      \
-  template cudaError_t launch_cell_pass<R>(const GridDims &, int, const R *, const R *, const R *,            \
-                                           const unsigned char *, const R *, R *, R *, R *, R *, void *,       \
-                                           cudaStream_t);                                                       \
-  template cudaError_t launch_floor_fix<R>(long long, const R *, long long, const void *, double, R *,        \
-                                           cudaStream_t);                                                       \
+#define VET_INSTANTIATE(R)                                                                                   \
+  template cudaError_t launch_face_level<R>(const GridDims &, const R *, const R *, const unsigned char *,   \
+                                            const FaceItem *, int, int, R *, const R *, long long, int *,   \
+                                            cudaStream_t);                                                   \
+  template cudaError_t launch_cell_pass<R>(const GridDims &, int, const R *, const R *, const unsigned char *, \
+                                           const int *, const R *, const R *, R *, R *, R *, R *, void *,    \
+                                           long long, int *, cudaStream_t);                                  \
+  template cudaError_t launch_fill_boundary<R>(const GridDims &, const unsigned char *, const R *, R *,      \
+                                               cudaStream_t);                                                \
+  template cudaError_t launch_floor_fix<R>(long long, const R *, long long, const void *, double, R *,     \
+                                           cudaStream_t);                                                    \
   template cudaError_t launch_moments<R>(long long, int, const R *, const R *, R *, cudaStream_t);
 
 VET_INSTANTIATE(float)

@@ -44,7 +44,7 @@ class _Grid(ctypes.Structure):
 
 class _Config(ctypes.Structure):
     _fields_ = [("nside", ctypes.c_int), ("rot_q", ctypes.c_double * 4), ("precision", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("spin_limit", ctypes.c_longlong)]
 
 
 _lib = None
@@ -139,7 +139,7 @@ class Context:
     """A libvet context: grid, direction set, templates and workspace."""
 
     def __init__(self, shape, block: int, h: float, nside: int, rot_q=(1.0, 0.0, 0.0, 0.0),
-                 precision: int = VET_FP32, device: int = 0):
+                 precision: int = VET_FP32, device: int = 0, spin_limit: int = 0):
         self._lib = load()
         nz, ny, nx = shape
         self.shape = (int(nz), int(ny), int(nx))
@@ -148,7 +148,7 @@ class Context:
         self.dtype = np.float64 if precision == VET_FP64 else np.float32
         g = _Grid(int(nx), int(ny), int(nz), int(block), float(h))
         q = (ctypes.c_double * 4)(*[float(v) for v in rot_q])
-        cfg = _Config(int(nside), q, int(precision), int(device))
+        cfg = _Config(int(nside), q, int(precision), int(device), int(spin_limit))
         h_ = ctypes.c_void_p()
         st = self._lib.vet_create(ctypes.byref(h_), ctypes.byref(g), ctypes.byref(cfg))
         if st != VET_OK:
