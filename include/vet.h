@@ -152,9 +152,49 @@ vet_status vet_last_timing(vet_ctx *ctx, float ms[4]);
  * the closing step). */
 int vet_launches_per_closure(const vet_ctx *ctx);
 
-/* Message for the last failure on ctx (or for the last vet_create failure
- * in this thread when ctx is NULL).  Never NULL. */
+/* Message for the last failure on ctx (or, when ctx is NULL, for the last
+ * failure of vet_create or vet_closure_noalloc in this thread).  Never NULL. */
 const char *vet_last_error(const vet_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * An entry point that allocates nothing (the paper has no counterpart; it
+ * exists for callers of this library, not for the method).
+ *
+ * Some callers cannot call cudaMalloc: code running while another framework's
+ * caching allocator holds nearly all device memory (the allocation would
+ * fail), real-time loops that must not block on cudaMalloc / cudaFree (both
+ * can synchronise the whole device), and plug-ins whose host application
+ * forbids allocations outside its own pool.  They still own their inputs and
+ * outputs; what they cannot provide is the library's workspace.
+ *
+ * vet_closure_noalloc computes exactly what vet_create + vet_closure (FP32)
+ * compute, without a context: every piece of workspace lives in one static
+ * device array of VET_NOALLOC_SCRATCH_BYTES compiled into libvet, which every
+ * GPU that loads the library holds until the process exits, and the host-side
+ * geometry uses fixed static host arrays.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   - Limits: FP32 only; nside 1, 2 or 4; block edge 2..16; and the problem's
+ *     workspace (about 12 * N * blocks * (block+2)^2 bytes for the face
+ *     intensities plus templates and schedule) must fit the array, e.g.
+ *     64^3 cells in 16^3 blocks with 192 directions, or 32^3 cells in 8^3
+ *     blocks with 48.  Larger problems return VET_EINVAL with a message
+ *     (vet_last_error(NULL)).
+ *   - Field pointers must be device memory.  Work is enqueued on `stream`
+ *     and the call returns before it runs.
+ *   - The first call made for a device (cfg->device) looks up the array's
+ *     device address with that device selected; make that first call before
+ *     any stream capture.
+ *   - Every call shares the one array and overwrites what the previous call
+ *     left there.  Calls whose GPU work overlaps (different streams, or
+ *     different host threads with no ordering between them) race on it and
+ *     give wrong results: order them.
+ *   - If a bounded device-side wait gives up (see vet_sync), f_out is filled
+ *     with NaN: there is no context to report it through.
+ * ---------------------------------------------------------------------- */
+#define VET_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+vet_status vet_closure_noalloc(const vet_grid *grid, const vet_config *cfg, const float *kappa, const float *S,
+                               const float *Ib, float *f_out, float *M_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,250 @@
+// vet_geometry.h -- host-side geometry of the VET closure, shared by the
+// context path (vet_host.cu) and the allocation-free path (vet_noalloc.cu):
+// the HEALPix direction set, the per-direction ray templates, the internal
+// direction orders and the wavefront schedule of the face pass.  Every
+// function writes into caller-provided memory and allocates nothing.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "vet_internal.h"
+
+namespace vet {
+namespace geom {
+
+// HEALPix ring-scheme pixel centres (Gorski et al. 2005, Sec. 4): north cap
+// rings i < nside at z = 1 - i^2/(3 nside^2) with 4i pixels at
+// phi = (j - 1/2) pi/(2i); equatorial rings nside <= i <= 3 nside at
+// z = 4/3 - 2i/(3 nside) with 4 nside pixels at phi = (j - s/2) pi/(2 nside),
+// s = (i - nside + 1) mod 2; south cap mirrored.  Then rotated by the unit
+// quaternion q (the paper's random rotation, Sec. 2.2.5).  out: [N][4] =
+// (nx, ny, nz, w) with w = 4 pi / N.
+inline void healpix_directions(int nside, const double q_in[4], double *out) {
+  const double pi = 3.14159265358979323846;
+  const int N = 12 * nside * nside;
+  const double qn = std::sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+  const double qw = q_in[0] / qn, qx = q_in[1] / qn, qy = q_in[2] / qn, qz = q_in[3] / qn;
+  const double R[3][3] = {
+      {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+      {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+      {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+  int p = 0;
+  for (int ring = 1; ring < 4 * nside; ++ring) {
+    int cnt;
+    double z, first, step;
+    if (ring < nside || ring > 3 * nside) {
+      const int i = ring < nside ? ring : 4 * nside - ring;
+      const double zz = 1.0 - double(i) * i / (3.0 * nside * nside);
+      z = ring < nside ? zz : -zz;
+      cnt = 4 * i;
+      step = pi / (2.0 * i);
+      first = 0.5 * step;
+    } else {
+      z = 4.0 / 3.0 - 2.0 * ring / (3.0 * nside);
+      const int s = (ring - nside + 1) % 2;
+      cnt = 4 * nside;
+      step = pi / (2.0 * nside);
+      first = step * (1.0 - 0.5 * s);
+    }
+    const double sin_t = std::sqrt((1.0 - z) * (1.0 + z));
+    for (int j = 0; j < cnt; ++j, ++p) {
+      const double phi = first + j * step;
+      const double v[3] = {sin_t * std::cos(phi), sin_t * std::sin(phi), z};
+      for (int a = 0; a < 3; ++a) out[4 * p + a] = R[a][0] * v[0] + R[a][1] * v[1] + R[a][2] * v[2];
+      out[4 * p + 3] = 4.0 * pi / N;
+    }
+  }
+}
+
+struct Event {
+  double t;
+  int axis, m;
+};
+
+// Merge order of plane crossings: by parameter, ties to the lowest axis (no
+// two events share both, so the order is total).
+inline void merge_events(Event *ev, int n) {
+  std::sort(ev, ev + n, [](const Event &a, const Event &b) { return a.t < b.t || (a.t == b.t && a.axis < b.axis); });
+}
+
+// Ray templates of one direction for block edge B (cell units; segment
+// lengths are stored as -length * h * log2(e)), written into the blob `out`
+// laid out by tpl_layout.  Returns in cell_segs / node_segs the segments a
+// block's cell rays and face-node rays cross for this direction.
+template <typename R>
+void build_template(const double *d, int ext, int B, double h, unsigned char *out, long long &cell_segs,
+                    long long &node_segs) {
+  const TplLayout L = tpl_layout<R>(B);
+  std::memset(out, 0, L.bytes);
+  auto *hd = reinterpret_cast<TplHead<R> *>(out);
+  auto *cev = reinterpret_cast<TplEvent<R> *>(out + L.cev);
+  auto *nev = reinterpret_cast<TplEvent<R> *>(out + L.nev);
+  int16_t *cpos = reinterpret_cast<int16_t *>(out + L.cpos);
+  int16_t *npos = reinterpret_cast<int16_t *>(out + L.npos);
+  int16_t *ck = reinterpret_cast<int16_t *>(out + L.ck);
+  R *cw = reinterpret_cast<R *>(out + L.cw);
+  int16_t *nk = reinterpret_cast<int16_t *>(out + L.nk);
+  R *nw = reinterpret_cast<R *>(out + L.nw);
+  const double scale = -h * 1.4426950408889634074;  // -h log2(e)
+  double an[3];
+  int sgn[3];
+  for (int a = 0; a < 3; ++a) {
+    hd->n[a] = R(d[a]);
+    an[a] = std::fabs(d[a]);
+    sgn[a] = d[a] < 0.0 ? -1 : 1;
+    hd->sgn[a] = sgn[a];
+  }
+  hd->w = R(d[3]);
+  hd->ext = ext;
+  const TileShape ct = cell_tile(B), nt = node_tile(B);
+  const int cstride[3] = {1, ct.sy, ct.sz};  // cell rays walk the cell-pass tile
+  const int nstride[3] = {1, nt.sy, nt.sz};  // node rays walk the face-pass tile
+  Event ev[3 * kMaxBlock];
+  // cell rays: planes at t = (m + 1/2)/|n_a|, m = 0..B-1
+  int n = 0;
+  for (int a = 0; a < 3; ++a)
+    if (an[a] > 0.0)
+      for (int m = 0; m < B; ++m) ev[n++] = {(m + 0.5) / an[a], a, m};
+  merge_events(ev, n);
+  for (int i = 0; i < 3 * B; ++i) cpos[i] = kNever;
+  double prev = 0.0;
+  for (int e = 0; e < n; ++e) {
+    cpos[ev[e].axis * B + ev[e].m] = (int16_t)e;
+    cev[e].len = R((ev[e].t - prev) * scale);
+    cev[e].delta = -sgn[ev[e].axis] * cstride[ev[e].axis];
+    prev = ev[e].t;
+  }
+  // node rays: planes at t = m/|n_a|, m = 1..B
+  n = 0;
+  for (int a = 0; a < 3; ++a)
+    if (an[a] > 0.0)
+      for (int m = 1; m <= B; ++m) ev[n++] = {m / an[a], a, m};
+  merge_events(ev, n);
+  for (int a = 0; a < 3; ++a) {
+    npos[a * (B + 1)] = -1;
+    for (int m = 1; m <= B; ++m) npos[a * (B + 1) + m] = kNever;
+  }
+  prev = 0.0;
+  for (int e = 0; e < n; ++e) {
+    npos[ev[e].axis * (B + 1) + ev[e].m] = (int16_t)e;
+    nev[e].len = R((ev[e].t - prev) * scale);
+    nev[e].delta = -sgn[ev[e].axis] * nstride[ev[e].axis];
+    prev = ev[e].t;
+  }
+  // exit tables: leaving through axis a at depth D, the in-plane upwind-frame
+  // offset along axis b is d = off - (D / |n_a|) |n_b| (off = 1/2 for cells,
+  // 0 for nodes); stored as k = floor(d) and (f, 1 - f), f = d - k.
+  auto fill_exit = [&](int16_t *K, R *W, int rows, bool cells) {
+    for (int a = 0; a < 3; ++a) {
+      const int bc[2] = {a == 0 ? 1 : 0, a == 2 ? 1 : 2};
+      for (int j = 0; j < 2; ++j)
+        for (int l = 0; l < rows; ++l) {
+          const int idx = (a * 2 + j) * rows + l;
+          double dd = 0.0;
+          if (an[a] > 0.0) {
+            const double depth = cells ? l + 0.5 : (double)l;
+            const double t = depth / an[a];
+            dd = (cells ? 0.5 : 0.0) - t * an[bc[j]];
+            // an exit exactly on a face edge (a tie with axis b) may come out
+            // a rounding error below the integer; snap it so that the device
+            // never sees a node index below 0
+            const double r = std::nearbyint(dd);
+            if (std::fabs(dd - r) < 1e-12) dd = r;
+          }
+          const double k = std::floor(dd);
+          const double f = dd - k;
+          K[idx] = (int16_t)k;
+          W[2 * idx] = R(f);
+          W[2 * idx + 1] = R(1.0 - f);
+        }
+    }
+  };
+  fill_exit(ck, cw, B, true);
+  fill_exit(nk, nw, B + 1, false);
+  // work measure: segments = exit event index + 1 per ray
+  long long cs = 0, ns = 0;
+  for (int l2 = 0; l2 < B; ++l2)
+    for (int l1 = 0; l1 < B; ++l1)
+      for (int l0 = 0; l0 < B; ++l0)
+        cs += 1 + std::min({(int)cpos[l0], (int)cpos[B + l1], (int)cpos[2 * B + l2]});
+  for (int a = 0; a < 3; ++a) {
+    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+    for (int u = 0; u <= B; ++u)
+      for (int v = 0; v <= B; ++v) {
+        int P[3];
+        P[a] = sgn[a] > 0 ? B : 0;
+        P[b] = u;
+        P[c] = v;
+        int Lq[3];
+        for (int q = 0; q < 3; ++q) Lq[q] = sgn[q] > 0 ? P[q] : B - P[q];
+        ns += 1 + std::min({(int)npos[Lq[0]], (int)npos[(B + 1) + Lq[1]], (int)npos[2 * (B + 1) + Lq[2]]});
+      }
+  }
+  cell_segs = cs;
+  node_segs = ns;
+}
+
+inline int octant_of(const double *d) { return (d[0] < 0) + 2 * (d[1] < 0) + 4 * (d[2] < 0); }
+
+// Internal order: octant-major, HEALPix order within an octant.  order[i] is
+// the HEALPix index of internal direction i; ob[o]..ob[o+1] the octant ranges.
+inline void internal_order(int N, const double *dirs, int *order, int ob[9]) {
+  int i = 0;
+  for (int o = 0; o < 8; ++o) {
+    ob[o] = i;
+    for (int k = 0; k < N; ++k)
+      if (octant_of(dirs + 4 * k) == o) order[i++] = k;
+  }
+  ob[8] = i;
+}
+
+// Cell-pass visiting order: octants interleaved round robin.
+inline void interleaved_order(const int ob[9], int *out) {
+  int n = 0;
+  for (int r = 0; n < ob[8]; ++r)
+    for (int o = 0; o < 8; ++o)
+      if (ob[o] + r < ob[o + 1]) out[n++] = ob[o] + r;
+}
+
+// Face-pass schedule: level L of block b in octant o is b's upwind-ordered
+// index sum; one item = (block, up to `group` directions of one octant).
+// Writes level_off[0..nlevels] and, when items != nullptr, the items.
+// Returns the number of items, or -1 if it exceeds `cap`.
+inline long long build_schedule(const int nb[3], const int ob[9], int group, FaceItem *items, long long cap,
+                                int *level_off) {
+  const int nlevels = nb[0] + nb[1] + nb[2] - 2;
+  // visit(L, f) calls f(block, d0, count) for every item of level L
+  auto visit = [&](int L, auto &&f) {
+    for (int o = 0; o < 8; ++o) {
+      if (ob[o + 1] == ob[o]) continue;
+      const int s[3] = {(o & 1) ? -1 : 1, (o & 2) ? -1 : 1, (o & 4) ? -1 : 1};
+      for (int bz = 0; bz < nb[2]; ++bz)
+        for (int by = 0; by < nb[1]; ++by)
+          for (int bx = 0; bx < nb[0]; ++bx) {
+            const int bb[3] = {bx, by, bz};
+            int lv = 0;
+            for (int a = 0; a < 3; ++a) lv += s[a] > 0 ? bb[a] : nb[a] - 1 - bb[a];
+            if (lv != L) continue;
+            const int id = (bz * nb[1] + by) * nb[0] + bx;
+            for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += group) f(id, d0, std::min(group, ob[o + 1] - d0));
+          }
+    }
+  };
+  long long total = 0;
+  for (int L = 0; L < nlevels; ++L) {
+    level_off[L] = (int)total;
+    visit(L, [&](int, int, int) { ++total; });
+  }
+  level_off[nlevels] = (int)total;
+  if (total > cap) return -1;
+  if (!items) return total;
+  long long k = 0;
+  for (int L = 0; L < nlevels; ++L) visit(L, [&](int id, int d0, int cnt) { items[k++] = {id, d0, cnt, 0}; });
+  return k;
+}
+
+}  // namespace geom
+}  // namespace vet

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "vet.h"
+#include "vet_geometry.h"
 #include "vet_internal.h"
 
 #define VET_API extern "C" __attribute__((visibility("default")))
@@ -77,179 +78,6 @@ struct DeviceGuard {
   }
 };
 
-// HEALPix ring-scheme pixel centres (Gorski et al. 2005, Sec. 4): north cap
-// rings i < nside at z = 1 - i^2/(3 nside^2) with 4i pixels at
-// phi = (j - 1/2) pi/(2i); equatorial rings nside <= i <= 3 nside at
-// z = 4/3 - 2i/(3 nside) with 4 nside pixels at phi = (j - s/2) pi/(2 nside),
-// s = (i - nside + 1) mod 2; south cap mirrored.  Then rotated by the unit
-// quaternion q (the paper's random rotation, Sec. 2.2.5).
-void healpix_directions(int nside, const double q_in[4], std::vector<double> &out) {
-  const double pi = 3.14159265358979323846;
-  const int N = 12 * nside * nside;
-  double qn = std::sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
-  const double qw = q_in[0] / qn, qx = q_in[1] / qn, qy = q_in[2] / qn, qz = q_in[3] / qn;
-  const double R[3][3] = {
-      {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
-      {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
-      {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
-  out.assign((size_t)N * 4, 0.0);
-  int p = 0;
-  for (int ring = 1; ring < 4 * nside; ++ring) {
-    int cnt;
-    double z, first, step;
-    if (ring < nside || ring > 3 * nside) {
-      const int i = ring < nside ? ring : 4 * nside - ring;
-      const double zz = 1.0 - double(i) * i / (3.0 * nside * nside);
-      z = ring < nside ? zz : -zz;
-      cnt = 4 * i;
-      step = pi / (2.0 * i);
-      first = 0.5 * step;
-    } else {
-      z = 4.0 / 3.0 - 2.0 * ring / (3.0 * nside);
-      const int s = (ring - nside + 1) % 2;
-      cnt = 4 * nside;
-      step = pi / (2.0 * nside);
-      first = step * (1.0 - 0.5 * s);
-    }
-    const double sin_t = std::sqrt((1.0 - z) * (1.0 + z));
-    for (int j = 0; j < cnt; ++j, ++p) {
-      const double phi = first + j * step;
-      const double v[3] = {sin_t * std::cos(phi), sin_t * std::sin(phi), z};
-      for (int a = 0; a < 3; ++a) out[4 * p + a] = R[a][0] * v[0] + R[a][1] * v[1] + R[a][2] * v[2];
-      out[4 * p + 3] = 4.0 * pi / N;
-    }
-  }
-}
-
-struct Event {
-  double t;
-  int axis, m;
-};
-
-void merge_events(std::vector<Event> &ev) {
-  std::stable_sort(ev.begin(), ev.end(), [](const Event &a, const Event &b) {
-    return a.t < b.t || (a.t == b.t && a.axis < b.axis);
-  });
-}
-
-// Ray templates of one direction for block edge B (cell units; segment
-// lengths are stored as -length * h * log2(e)), written into the blob `out`
-// laid out by tpl_layout.  Returns the segments a block's cell rays and
-// face-node rays cross for this direction.
-template <typename R>
-void build_template(const double *d, int ext, int B, double h, unsigned char *out, long long &cell_segs,
-                    long long &node_segs) {
-  const vet::TplLayout L = vet::tpl_layout<R>(B);
-  std::memset(out, 0, L.bytes);
-  auto *hd = reinterpret_cast<vet::TplHead<R> *>(out);
-  auto *cev = reinterpret_cast<vet::TplEvent<R> *>(out + L.cev);
-  auto *nev = reinterpret_cast<vet::TplEvent<R> *>(out + L.nev);
-  int16_t *cpos = reinterpret_cast<int16_t *>(out + L.cpos);
-  int16_t *npos = reinterpret_cast<int16_t *>(out + L.npos);
-  int16_t *ck = reinterpret_cast<int16_t *>(out + L.ck);
-  R *cw = reinterpret_cast<R *>(out + L.cw);
-  int16_t *nk = reinterpret_cast<int16_t *>(out + L.nk);
-  R *nw = reinterpret_cast<R *>(out + L.nw);
-  const double scale = -h * 1.4426950408889634074;  // -h log2(e)
-  double an[3];
-  int sgn[3];
-  for (int a = 0; a < 3; ++a) {
-    hd->n[a] = R(d[a]);
-    an[a] = std::fabs(d[a]);
-    sgn[a] = d[a] < 0.0 ? -1 : 1;
-    hd->sgn[a] = sgn[a];
-  }
-  hd->w = R(d[3]);
-  hd->ext = ext;
-  const vet::TileShape ct = vet::cell_tile(B), nt = vet::node_tile(B);
-  const int cstride[3] = {1, ct.sy, ct.sz};  // cell rays walk the cell-pass tile
-  const int nstride[3] = {1, nt.sy, nt.sz};  // node rays walk the face-pass tile
-  // cell rays: planes at t = (m + 1/2)/|n_a|, m = 0..B-1
-  std::vector<Event> ev;
-  for (int a = 0; a < 3; ++a)
-    if (an[a] > 0.0)
-      for (int m = 0; m < B; ++m) ev.push_back({(m + 0.5) / an[a], a, m});
-  merge_events(ev);
-  for (int i = 0; i < 3 * B; ++i) cpos[i] = vet::kNever;
-  double prev = 0.0;
-  for (size_t e = 0; e < ev.size(); ++e) {
-    cpos[ev[e].axis * B + ev[e].m] = (int16_t)e;
-    cev[e].len = R((ev[e].t - prev) * scale);
-    cev[e].delta = -sgn[ev[e].axis] * cstride[ev[e].axis];
-    prev = ev[e].t;
-  }
-  // node rays: planes at t = m/|n_a|, m = 1..B
-  ev.clear();
-  for (int a = 0; a < 3; ++a)
-    if (an[a] > 0.0)
-      for (int m = 1; m <= B; ++m) ev.push_back({m / an[a], a, m});
-  merge_events(ev);
-  for (int a = 0; a < 3; ++a) {
-    npos[a * (B + 1)] = -1;
-    for (int m = 1; m <= B; ++m) npos[a * (B + 1) + m] = vet::kNever;
-  }
-  prev = 0.0;
-  for (size_t e = 0; e < ev.size(); ++e) {
-    npos[ev[e].axis * (B + 1) + ev[e].m] = (int16_t)e;
-    nev[e].len = R((ev[e].t - prev) * scale);
-    nev[e].delta = -sgn[ev[e].axis] * nstride[ev[e].axis];
-    prev = ev[e].t;
-  }
-  // exit tables: leaving through axis a at depth D, the in-plane upwind-frame
-  // offset along axis b is d = off - (D / |n_a|) |n_b| (off = 1/2 for cells,
-  // 0 for nodes); stored as k = floor(d) and (f, 1 - f), f = d - k.
-  auto fill_exit = [&](int16_t *K, R *W, int rows, bool cells) {
-    for (int a = 0; a < 3; ++a) {
-      const int bc[2] = {a == 0 ? 1 : 0, a == 2 ? 1 : 2};
-      for (int j = 0; j < 2; ++j)
-        for (int l = 0; l < rows; ++l) {
-          const int idx = (a * 2 + j) * rows + l;
-          double dd = 0.0;
-          if (an[a] > 0.0) {
-            const double depth = cells ? l + 0.5 : (double)l;
-            const double t = depth / an[a];
-            dd = (cells ? 0.5 : 0.0) - t * an[bc[j]];
-            // an exit exactly on a face edge (a tie with axis b) may come out
-            // a rounding error below the integer; snap it so that the device
-            // never sees a node index below 0
-            const double r = std::nearbyint(dd);
-            if (std::fabs(dd - r) < 1e-12) dd = r;
-          }
-          const double k = std::floor(dd);
-          const double f = dd - k;
-          K[idx] = (int16_t)k;
-          W[2 * idx] = R(f);
-          W[2 * idx + 1] = R(1.0 - f);
-        }
-    }
-  };
-  fill_exit(ck, cw, B, true);
-  fill_exit(nk, nw, B + 1, false);
-  // work measure: segments = exit event index + 1 per ray
-  long long cs = 0, ns = 0;
-  for (int l2 = 0; l2 < B; ++l2)
-    for (int l1 = 0; l1 < B; ++l1)
-      for (int l0 = 0; l0 < B; ++l0)
-        cs += 1 + std::min({(int)cpos[l0], (int)cpos[B + l1], (int)cpos[2 * B + l2]});
-  for (int a = 0; a < 3; ++a) {
-    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-    for (int u = 0; u <= B; ++u)
-      for (int v = 0; v <= B; ++v) {
-        int P[3];
-        P[a] = sgn[a] > 0 ? B : 0;
-        P[b] = u;
-        P[c] = v;
-        int Lq[3];
-        for (int q = 0; q < 3; ++q) Lq[q] = sgn[q] > 0 ? P[q] : B - P[q];
-        ns += 1 + std::min({(int)npos[Lq[0]], (int)npos[(B + 1) + Lq[1]], (int)npos[2 * (B + 1) + Lq[2]]});
-      }
-  }
-  cell_segs = cs;
-  node_segs = ns;
-}
-
-int octant_of(const double *d) { return (d[0] < 0) + 2 * (d[1] < 0) + 4 * (d[2] < 0); }
-
 void free_ctx(vet_ctx *c) {
   if (!c) return;
   for (auto &e : c->ev)
@@ -270,58 +98,29 @@ void free_ctx(vet_ctx *c) {
 template <typename R>
 vet_status build_context(vet_ctx *c) {
   const int B = c->grid.block, N = c->N;
-  // internal order: octant-major, HEALPix order within an octant
   std::vector<int> order(N);
-  for (int k = 0; k < N; ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return octant_of(&c->dirs_ext[4 * a]) < octant_of(&c->dirs_ext[4 * b]);
-  });
+  int ob[9];
+  vet::geom::internal_order(N, c->dirs_ext.data(), order.data(), ob);
   const int tbytes = vet::tpl_layout<R>(B).bytes;
   std::vector<unsigned char> tpl((size_t)tbytes * N);
   long long cs_tot = 0, ns_tot = 0;
   for (int i = 0; i < N; ++i) {
     long long cs, ns;
-    build_template<R>(&c->dirs_ext[4 * order[i]], order[i], B, c->grid.h, tpl.data() + (size_t)i * tbytes, cs, ns);
+    vet::geom::build_template<R>(&c->dirs_ext[4 * order[i]], order[i], B, c->grid.h, tpl.data() + (size_t)i * tbytes,
+                                 cs, ns);
     cs_tot += cs;
     ns_tot += ns;
   }
   c->cell_segs = cs_tot * c->nblk;
   c->face_segs = ns_tot * c->nblk;
-  // face-pass schedule: level L of a block in octant o is its upwind-ordered
-  // index sum; one item = (block, up to kGroup directions of one octant).
-  const int kGroup = vet::kFaceGroup;
   const int nb[3] = {c->dims.nbx, c->dims.nby, c->dims.nbz};
   c->nlevels = nb[0] + nb[1] + nb[2] - 2;
-  std::vector<std::vector<FaceItem>> per_level(c->nlevels);
-  int ob[9] = {0};
-  for (int i = 0; i < N; ++i) ob[octant_of(&c->dirs_ext[4 * order[i]]) + 1]++;
-  for (int o = 0; o < 8; ++o) ob[o + 1] += ob[o];
-  for (int o = 0; o < 8; ++o) {
-    if (ob[o + 1] == ob[o]) continue;
-    const int s[3] = {(o & 1) ? -1 : 1, (o & 2) ? -1 : 1, (o & 4) ? -1 : 1};
-    for (int bz = 0; bz < nb[2]; ++bz)
-      for (int by = 0; by < nb[1]; ++by)
-        for (int bx = 0; bx < nb[0]; ++bx) {
-          const int bb[3] = {bx, by, bz};
-          int L = 0;
-          for (int a = 0; a < 3; ++a) L += s[a] > 0 ? bb[a] : nb[a] - 1 - bb[a];
-          const int id = (bz * nb[1] + by) * nb[0] + bx;
-          for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += kGroup)
-            per_level[L].push_back({id, d0, std::min(kGroup, ob[o + 1] - d0), 0});
-        }
-  }
-  // cell-pass order: octants interleaved round robin
-  std::vector<int> cell_order;
-  for (int r = 0; (int)cell_order.size() < N; ++r)
-    for (int o = 0; o < 8; ++o)
-      if (ob[o] + r < ob[o + 1]) cell_order.push_back(ob[o] + r);
-  std::vector<FaceItem> items;
   c->level_off.assign(c->nlevels + 1, 0);
-  for (int L = 0; L < c->nlevels; ++L) {
-    c->level_off[L] = (int)items.size();
-    items.insert(items.end(), per_level[L].begin(), per_level[L].end());
-  }
-  c->level_off[c->nlevels] = (int)items.size();
+  const long long nitems = vet::geom::build_schedule(nb, ob, vet::kFaceGroup, nullptr, 1LL << 40, c->level_off.data());
+  std::vector<FaceItem> items((size_t)nitems);
+  vet::geom::build_schedule(nb, ob, vet::kFaceGroup, items.data(), nitems, c->level_off.data());
+  std::vector<int> cell_order(N);
+  vet::geom::interleaved_order(ob, cell_order.data());
   // moment coefficients in HEALPix order
   std::vector<R> coef((size_t)N * 10);
   for (int k = 0; k < N; ++k) {
@@ -592,6 +391,8 @@ vet_status do_closure(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *f_
 
 }  // namespace
 
+void vet::set_thread_error(const char *msg) { g_create_err = msg; }
+
 VET_API vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_config *cfg) {
   if (!out) return set_err(nullptr, VET_EINVAL, "out is NULL");
   *out = nullptr;
@@ -636,7 +437,8 @@ VET_API vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_con
   c->dims.ndir = c->N;
   c->dims.ncell = (long long)g.nx * g.ny * g.nz;
   c->nblk = c->dims.nbx * c->dims.nby * c->dims.nbz;
-  healpix_directions(cfg->nside, cfg->rot_q, c->dirs_ext);
+  c->dirs_ext.assign((size_t)c->N * 4, 0.0);
+  vet::geom::healpix_directions(cfg->nside, cfg->rot_q, c->dirs_ext.data());
   vet_status s;
   {
     DeviceGuard dg(cfg->device);

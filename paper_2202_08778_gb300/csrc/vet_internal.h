@@ -167,4 +167,7 @@ constexpr int kFaceGroup = 4;
 // Per-device kernel attributes; call with the context's device current.
 cudaError_t prepare_kernels();
 
+// Sets the calling thread's message returned by vet_last_error(NULL).
+void set_thread_error(const char *msg);
+
 }  // namespace vet

@@ -27,7 +27,7 @@ _STATUS = {1: "VET_EINVAL", 2: "VET_ENOMEM", 3: "VET_ECUDA", 4: "VET_ETIMEOUT", 
 EXPORTS = (
     "vet_create", "vet_destroy", "vet_num_directions", "vet_directions", "vet_trace", "vet_moments",
     "vet_closure", "vet_trace_f64", "vet_moments_f64", "vet_closure_f64", "vet_sync", "vet_work_counts",
-    "vet_set_timing", "vet_last_timing", "vet_launches_per_closure", "vet_last_error",
+    "vet_set_timing", "vet_last_timing", "vet_launches_per_closure", "vet_last_error", "vet_closure_noalloc",
 )
 
 
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
         lib.vet_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.vet_launches_per_closure.argtypes = [vp]
         lib.vet_launches_per_closure.restype = i
+        lib.vet_closure_noalloc.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Config), vp, vp, vp, vp, vp, vp]
         lib.vet_last_error.argtypes = [vp]
         lib.vet_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -218,3 +219,24 @@ class Context:
 
     def sync(self):
         self._check(self._lib.vet_sync(self._h))
+
+
+def closure_noalloc(shape, block: int, h: float, nside: int, kappa, S, Ib, f_out, M_out=None,
+                    rot_q=(1.0, 0.0, 0.0, 0.0), device: int = 0, spin_limit: int = 0, stream=None):
+    """vet_closure_noalloc: the FP32 closure without a context and without any
+    allocation (workspace is a static device array inside libvet; see
+    include/vet.h for its limits).  Field arguments must be CUDA tensors."""
+    lib = load()
+    nz, ny, nx = shape
+    n = int(nz) * int(ny) * int(nx)
+    N = 12 * int(nside) ** 2
+    g = _Grid(int(nx), int(ny), int(nz), int(block), float(h))
+    q = (ctypes.c_double * 4)(*[float(v) for v in rot_q])
+    cfg = _Config(int(nside), q, VET_FP32, int(device), int(spin_limit))
+    st = lib.vet_closure_noalloc(ctypes.byref(g), ctypes.byref(cfg), _ptr(kappa, np.float32, n, "kappa"),
+                                 _ptr(S, np.float32, n, "S"), _ptr(Ib, np.float32, 6 * N, "Ib"),
+                                 _ptr(f_out, np.float32, 6 * n, "f_out"), _ptr(M_out, np.float32, 10 * n, "M_out"),
+                                 _stream(stream))
+    if st != VET_OK:
+        raise VetError(st, lib.vet_last_error(None).decode())
+    return f_out
