@@ -45,6 +45,21 @@ def workload():
                "seed": 2, "boundary": "vacuum", "l2": "flushed between timed steps (256 MiB write)"}
 
 
+def measured_traffic():
+    """DRAM bytes per cell-pass launch from the committed ncu capture, or None
+    if the kernel source changed since the counters were taken."""
+    import hashlib
+
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "cell_pass_lognormal128_traffic.json")))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if hashlib.sha256(src).hexdigest() != rec.get("kernel_source_sha256"):
+        return None
+    return rec.get("bytes_per_launch")
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -235,13 +250,7 @@ def run_ours(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = MUFU_PER_CLK_PER_SM * N_SM * sm_max * 1e6 / 1e9  # G exp/s
     achieved = cell_segs / (cell_ms * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "cell_pass_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = measured_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G exp/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "cell_pass_kernel<float,0>",
                 "peak_basis": f"MUFU ex2: {MUFU_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {sm_max:.0f} MHz",
