@@ -10,11 +10,11 @@
  *      along a HEALPix set of N = 12 nside^2 directions (Sec. 2.2.5, App. B)
  *      with hybrid characteristics (long characteristics inside cubic blocks,
  *      bilinear interpolation of face intensities between blocks);
- *   2. take the angular quadratures (Eqs. 6-8 and the discrete sums of
+ *   2. take the angular quadratures (Eqs. 10-12 and the discrete sums of
  *      Sec. 2.2.5, with c = 1)
  *        E = sum_k w_k I_k,  F_i = sum_k w_k I_k n_ik,
  *        P_ij = sum_k w_k I_k n_ik n_jk,   w_k = 4 pi / N;
- *   3. form the Eddington tensor f_ij = P_ij / E                (Eq. 9).
+ *   3. form the Eddington tensor f_ij = P_ij / E                (Eq. 13).
  *
  * Conventions shared by every entry point
  *   - kappa is the absorption coefficient per unit length (the paper's
@@ -110,11 +110,11 @@ vet_status vet_directions(const vet_ctx *ctx, double *dirs_out);
 vet_status vet_trace(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, float *I_out,
                      void *stream);
 
-/* Angular quadratures of given intensities (Eqs. 6-8, c = 1):
+/* Angular quadratures of given intensities (Eqs. 10-12, c = 1):
  * I[N][cells] -> M_out[10][cells].  FP32 context only. */
 vet_status vet_moments(vet_ctx *ctx, const float *I, float *M_out, void *stream);
 
-/* Whole closure, fused: trace + quadratures + f = P/E (Eq. 9) without
+/* Whole closure, fused: trace + quadratures + f = P/E (Eq. 13) without
  * storing I.  f_out[6][cells] required; M_out[10][cells] optional (NULL).
  * FP32 context only. */
 vet_status vet_closure(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, float *f_out,

@@ -7,8 +7,8 @@ with the product library.
 Functions follow the paper's steps (VETTAM, Sec. 2.2.5):
   healpix   -- HEALPix direction set, equal weights 4 pi / N, rotated;
   trace     -- hybrid-characteristics formal solution of Eq. 14 (RTeq);
-  moments   -- E, F_i, P_ij quadratures (Eqs. 6-8, c = 1);
-  closure   -- f_ij = P_ij / E (Eq. 9) with the isotropic fallback where E
+  moments   -- E, F_i, P_ij quadratures (Eqs. 10-12, c = 1);
+  closure   -- f_ij = P_ij / E (Eq. 13) with the isotropic fallback where E
                does not exceed floor_rel * max E.
 """
 from __future__ import annotations

@@ -16,9 +16,9 @@
  *      dI/ds = kappa (S - I)  (Eq. 14, "RTeq"; kappa here already includes
  *      the density factor rho) along every direction, by hybrid
  *      characteristics on a grid split into cubic blocks (reading below);
- *   3. the angular quadratures E, F_i, P_ij (Eqs. 6-8 and the discrete sums
- *      of Sec. 2.2.5, with c = 1);
- *   4. the Eddington tensor f_ij = P_ij / E (Eq. 9, "closure").
+ *   3. the angular quadratures E, F_i, P_ij (Eqs. 10-12 and the discrete
+ *      sums of Sec. 2.2.5, Eqs. 55-56, with c = 1);
+ *   4. the Eddington tensor f_ij = P_ij / E (Eq. 13, "closure").
  *
  * Reading of "hybrid characteristics" (the paper names the method and cites
  * Buntemeyer et al. 2016 but gives no algorithm):
@@ -358,7 +358,7 @@ int ora_trace(const ora_grid *g, const double *dirs, int ndir, const double *kap
 }
 
 /* ------------------------------------------------------------------------ */
-/* 3. Angular quadratures (Sec. 2.2.5 sums; Eqs. 6-8 with c = 1):            */
+/* 3. Angular quadratures (Sec. 2.2.5 sums; Eqs. 10-12 with c = 1):            */
 /*    E = sum_k w_k I_k, F_i = sum_k w_k I_k n_ik,                            */
 /*    P_ij = sum_k w_k I_k n_ik n_jk.                                         */
 /*    M [10][cells] = E, Fx, Fy, Fz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz.            */
@@ -387,7 +387,7 @@ int ora_moments(const double *I, const double *dirs, int ndir, long ncell, doubl
 }
 
 /* ------------------------------------------------------------------------ */
-/* 4. Closure (Eq. 9): f_ij = P_ij / E.  Cells whose E does not exceed       */
+/* 4. Closure (Eq. 13): f_ij = P_ij / E.  Cells whose E does not exceed       */
 /*    E_floor = floor_rel * max_cells E receive the isotropic tensor I/3 and */
 /*    flag[c] = 1 (E = 0 happens where no radiation reaches a cell).         */
 /*    f [6][cells] = xx, yy, zz, xy, xz, yz.                                  */

@@ -8,9 +8,9 @@
 //                 the upwind neighbours' face nodes are bilinearly
 //                 interpolated (hybrid characteristics);
 //   cell pass  -- fully parallel: every cell-centre ray of a block for every
-//                 direction, with the quadratures E, F, P (Eqs. 6-8)
+//                 direction, with the quadratures E, F, P (Eqs. 10-12)
 //                 accumulated in registers across all directions and
-//                 f = P/E (Eq. 9) in the epilogue, so that I is never stored.
+//                 f = P/E (Eq. 13) in the epilogue, so that I is never stored.
 // Both passes stage the block's kappa/S tile, the directions' ray templates
 // and the incoming faces in shared memory.  Faces are stored by the face pass
 // already in the consumer's upwind frame and padded, so staging is a plain

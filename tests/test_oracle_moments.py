@@ -1,5 +1,5 @@
-"""Pins for the oracle's angular quadratures (VETTAM Eqs. 6-8 and the
-discrete sums of Sec. 2.2.5, c = 1) and closure f = P/E (Eq. 9)."""
+"""Pins for the oracle's angular quadratures (VETTAM Eqs. 10-12 and the
+discrete sums of Sec. 2.2.5, Eqs. 55-56, c = 1) and closure f = P/E (Eq. 13)."""
 import math
 
 import numpy as np

@@ -1,6 +1,6 @@
 """Pins for the oracle's formal solution of the gray transfer equation
 dI/ds = kappa (S - I) (VETTAM Eq. 14) by hybrid characteristics, and for its
-moments and closure (Eqs. 6-9).  Every expected value below comes from a
+moments and closure (Eqs. 10-13).  Every expected value below comes from a
 closed form, an invariant of the equation, or the brute-force integrator in
 tests/bruteforce.py -- never from the oracle itself."""
 import math
