@@ -127,7 +127,7 @@ struct FaceItem {
 // mbarrier); a wait that gives up ORs a code into *status and the kernel
 // returns early with its outputs incomplete.
 //   status bits: 1 face-pass staging, 2 cell-pass staging, 4 cell-pass buffer
-//   release.
+//   release, 8 the final wait for copies still in flight.
 
 // Face pass of one wavefront level: nitems items of at most max_dirs
 // directions each.

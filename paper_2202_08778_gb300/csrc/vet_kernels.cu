@@ -162,6 +162,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
   return false;
 }
 
+// The same wait taken by a whole warp (all 32 lanes converged): every lane
+// polls, but the warp stops only on a warp-wide decision, so either all lanes
+// see the phase complete or all give up together.  A per-lane decision could
+// let one lane leave a loop whose other lanes then wait forever at the next
+// warp-synchronous instruction.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, long long limit, int *status,
+                                               int code) {
+  const uint32_t a = smem_u32(bar);
+  bool done = false;
+  for (long long i = 0; i < limit; ++i) {
+    if (!done) {
+      uint32_t d;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(d)
+          : "r"(a), "r"(parity)
+          : "memory");
+      done = d != 0;
+    }
+    if (__all_sync(0xffffffffu, done)) return true;
+  }
+  if ((threadIdx.x & 31) == 0) atomicOr(status, code);
+  return false;
+}
+
+// Polls granted to the final wait for copies still in flight after another
+// wait gave up (status bit 8 if even that one gives up).
+constexpr long long kDrainPolls = 1LL << 22;
+
 // One bulk copy global -> shared (16-byte aligned addresses and size),
 // completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -276,7 +305,12 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
   }
   load_tile<R, BC>(tile, ts, g, bx, by, bz, kappa, S);
   __syncthreads();
-  if (!mbar_wait(&full, 0, spin_limit, status, 1)) return;
+  if (!mbar_wait_warp(&full, 0, spin_limit, status, 1)) {
+    // the copies this CTA issued must land before its shared memory is
+    // released: thread 0 waits for them once more (bounded) and all return
+    if (threadIdx.x == 0) mbar_wait(&full, 0, kDrainPolls, status, 8);
+    return;
+  }
   for (int w = threadIdx.x; w < it.dir_count * NN3; w += blockDim.x) {
     const int j = w / NN3, n = w - j * NN3;
     const Tpl<R> T(slots + sb * j, TL);
@@ -345,7 +379,9 @@ __global__ void __launch_bounds__(kCellThreads, 2)
   const int cpc = B3 / parts;  // cells of this CTA
   const int nwarps = blockDim.x >> 5;
   const int ntiles = (g.ndir + dt - 1) / dt;
+  int issued = 0, consumed = 0;   // thread 0's count of tiles issued / waited for
   auto issue_tile = [&](int t) {  // thread 0 only
+    issued = t + 1;
     const int b = t & 1, d0 = t * dt, nd = min(dt, g.ndir - d0);
     unsigned char *buf = buf0 + (size_t)b * dt * sb;
     mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
@@ -392,7 +428,8 @@ __global__ void __launch_bounds__(kCellThreads, 2)
   for (int t = 0; t < ntiles && ok; ++t) {
     const int b = t & 1;
     const uint32_t ph = (uint32_t)((t >> 1) & 1);
-    if (!mbar_wait(&full[b], ph, spin_limit, status, 2)) { ok = false; break; }
+    if (!mbar_wait_warp(&full[b], ph, spin_limit, status, 2)) { ok = false; break; }
+    consumed = t + 1;
     const int nd = min(dt, g.ndir - t * dt);
     const unsigned char *buf = buf0 + (size_t)b * dt * sb;
     if (active) {
@@ -438,10 +475,18 @@ __global__ void __launch_bounds__(kCellThreads, 2)
     }
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[b]);
+    bool prod_ok = true;
     if (threadIdx.x == 0 && t + 2 < ntiles) {
-      if (!mbar_wait(&empty[b], ph, spin_limit, status, 4)) { ok = false; break; }
-      issue_tile(t + 2);
+      prod_ok = mbar_wait(&empty[b], ph, spin_limit, status, 4);
+      if (prod_ok) issue_tile(t + 2);
     }
+    // warp 0 leaves together when its producer lane gave up
+    if (!__shfl_sync(0xffffffffu, prod_ok ? 1 : 0, 0)) { ok = false; break; }
+  }
+  if (threadIdx.x == 0) {
+    // after a wait gave up, tiles may still be in flight into this CTA's
+    // shared memory: wait (bounded) for every tile issued but not consumed
+    for (int t = consumed; t < issued; ++t) mbar_wait(&full[t & 1], (uint32_t)((t >> 1) & 1), kDrainPolls, status, 8);
   }
   if (MODE == 0) {
     R emax = R(0);
