@@ -33,9 +33,10 @@ template <typename R> using vec2_t = typename Vec2<R>::T;
 // y = -x log2(e) (segment lengths are stored pre-scaled by -h log2(e)).
 //   FP32: for x < 1/2 both come from a polynomial, 1 - 2^y = y q(y) with q of
 //   degree 5 fitted by weighted least squares (relative error 1.4e-9 in exact
-//   arithmetic, i.e. FP32 rounding dominates), accurate where 1 - e would
-//   cancel and more accurate than the MUFU; for x >= 1/2, e comes from the
-//   MUFU (ex2.approx) and 1 - e is well conditioned.
+//   arithmetic, i.e. FP32 rounding dominates): 1 - e would cancel there, and
+//   the MUFU's 1.5e-7 error on e compounds along long thin paths (1.1e-5 on I
+//   after ~300 thin segments of the shadow workload, measured); for x >= 1/2,
+//   e comes from the MUFU (ex2.approx) and 1 - e is well conditioned.
 //   FP64: the CUDA math library's exp2 and expm1.
 __device__ __forceinline__ void attenuation(float y, float &e, float &om) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
@@ -59,34 +60,28 @@ __device__ __forceinline__ void attenuation(double y, double &e, double &om) {
 // Exact update over piecewise-constant cells, marching backward from the
 // ray's start: after the loop, I(start) = acc + T * I(entry point).
 template <typename R>
+__device__ __forceinline__ void segment(const vec2_t<R> *__restrict__ tile, int &idx, const TplEvent<R> &ev, R &acc,
+                                        R &T) {
+  const vec2_t<R> ks = tile[idx];
+  idx += ev.delta;
+  R ex, om;
+  attenuation(ks.x * ev.len, ex, om);
+  acc = fma(ks.y * om, T, acc);
+  T *= ex;
+}
+
+template <typename R>
 __device__ __forceinline__ void march(const vec2_t<R> *__restrict__ tile, int idx, int last,
                                       const TplEvent<R> *__restrict__ ev, R &acc, R &T) {
   acc = R(0);
   T = R(1);
   int e = 0;
   for (; e < last; e += 2) {  // two segments per trip
-    const TplEvent<R> e0 = ev[e];
-    const vec2_t<R> k0 = tile[idx];
-    idx += e0.delta;
-    const TplEvent<R> e1 = ev[e + 1];
-    const vec2_t<R> k1 = tile[idx];
-    idx += e1.delta;
-    R x0, o0, x1, o1;
-    attenuation(k0.x * e0.len, x0, o0);
-    attenuation(k1.x * e1.len, x1, o1);
-    acc = fma(k0.y * o0, T, acc);
-    T *= x0;
-    acc = fma(k1.y * o1, T, acc);
-    T *= x1;
+    const TplEvent<R> e0 = ev[e], e1 = ev[e + 1];
+    segment<R>(tile, idx, e0, acc, T);
+    segment<R>(tile, idx, e1, acc, T);
   }
-  if (e == last) {
-    const TplEvent<R> e0 = ev[e];
-    const vec2_t<R> k0 = tile[idx];
-    R x0, o0;
-    attenuation(k0.x * e0.len, x0, o0);
-    acc = fma(k0.y * o0, T, acc);
-    T *= x0;
-  }
+  if (e == last) segment<R>(tile, idx, ev[e], acc, T);
 }
 
 // Typed view of one direction's template blob.
@@ -416,10 +411,13 @@ __global__ void __launch_bounds__(kCellThreads, 2)
   }
   const int tc = cx + ts.sy * cy + ts.sz * cz;  // tile index
   const long long gc = ((long long)(bz * B + cz) * g.ny + (by * B + cy)) * g.nx + (bx * B + cx);
-  // Moments accumulated over all directions.  E, Pxx, Pyy and Pzz (sums of
-  // positive terms that f_ii = P_ii / E depends on) carry a Kahan
-  // compensation term: plain sequential FP32 sums of N terms lose about
-  // N/2 ulp, which would dominate the error of f.
+  // Moments over all directions: a plain partial sum over the directions of
+  // one tile, folded into the totals once per tile.  The fold of E, Pxx, Pyy
+  // and Pzz (positive sums that f_ii = P_ii / E depends on) is Kahan
+  // compensated: plain sequential FP32 sums of N terms lose about N/2 ulp,
+  // which would dominate the error of f.  F is summed only when the caller
+  // asks for the moments (MODE 0).
+  constexpr bool kWantF = MODE == 0;
   R mom[10], cmp[4];
   for (int m = 0; m < 10; ++m) mom[m] = R(0);
   for (int m = 0; m < 4; ++m) cmp[m] = R(0);
@@ -433,6 +431,8 @@ __global__ void __launch_bounds__(kCellThreads, 2)
     const int nd = min(dt, g.ndir - t * dt);
     const unsigned char *buf = buf0 + (size_t)b * dt * sb;
     if (active) {
+      R part[10];
+      for (int m = 0; m < 10; ++m) part[m] = R(0);
       for (int j = 0; j < nd; ++j) {
         const Tpl<R> T(buf + sb * j, TL);
         const R *fin = reinterpret_cast<const R *>(buf + sb * j + TL.bytes);
@@ -455,22 +455,37 @@ __global__ void __launch_bounds__(kCellThreads, 2)
         } else {
           const R w = T.h->w, nx = T.h->n[0], ny = T.h->n[1], nz = T.h->n[2];
           const R wI = w * I, wIx = wI * nx, wIy = wI * ny, wIz = wI * nz;
-          const R term[4] = {wI, wIx * nx, wIy * ny, wIz * nz};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {  // E, Pxx, Pyy, Pzz: compensated
-            const int m = q == 0 ? 0 : 3 + q;
-            const R y = term[q] - cmp[q];
-            const R tt = mom[m] + y;
-            cmp[q] = (tt - mom[m]) - y;
-            mom[m] = tt;
+          part[0] += wI;
+          if (kWantF) {
+            part[1] += wIx;
+            part[2] += wIy;
+            part[3] += wIz;
           }
-          mom[1] += wIx;
-          mom[2] += wIy;
-          mom[3] += wIz;
-          mom[7] = fma(wIx, ny, mom[7]);
-          mom[8] = fma(wIx, nz, mom[8]);
-          mom[9] = fma(wIy, nz, mom[9]);
+          part[4] = fma(wIx, nx, part[4]);
+          part[5] = fma(wIy, ny, part[5]);
+          part[6] = fma(wIz, nz, part[6]);
+          part[7] = fma(wIx, ny, part[7]);
+          part[8] = fma(wIx, nz, part[8]);
+          part[9] = fma(wIy, nz, part[9]);
         }
+      }
+      if (MODE != 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // E, Pxx, Pyy, Pzz: compensated fold
+          const int m = q == 0 ? 0 : 3 + q;
+          const R y = part[m] - cmp[q];
+          const R tt = mom[m] + y;
+          cmp[q] = (tt - mom[m]) - y;
+          mom[m] = tt;
+        }
+        if (kWantF) {
+          mom[1] += part[1];
+          mom[2] += part[2];
+          mom[3] += part[3];
+        }
+        mom[7] += part[7];
+        mom[8] += part[8];
+        mom[9] += part[9];
       }
     }
     __syncwarp();
@@ -488,11 +503,11 @@ __global__ void __launch_bounds__(kCellThreads, 2)
     // shared memory: wait (bounded) for every tile issued but not consumed
     for (int t = consumed; t < issued; ++t) mbar_wait(&full[t & 1], (uint32_t)((t >> 1) & 1), kDrainPolls, status, 8);
   }
-  if (MODE == 0) {
+  if (MODE != 1) {
     R emax = R(0);
     if (active && ok) {
       const R E = mom[0];
-      if (M_out) {
+      if (kWantF) {
         for (int m = 0; m < 10; ++m) M_out[m * g.ncell + gc] = mom[m];
       } else {
         E_out[gc] = E;
@@ -604,7 +619,8 @@ cudaError_t set_smem_attrs() {
                        (const void *)face_pass_kernel<R, 0>,       (const void *)cell_pass_kernel<R, 0, 8>,
                        (const void *)cell_pass_kernel<R, 0, 16>,   (const void *)cell_pass_kernel<R, 0, 0>,
                        (const void *)cell_pass_kernel<R, 1, 8>,    (const void *)cell_pass_kernel<R, 1, 16>,
-                       (const void *)cell_pass_kernel<R, 1, 0>};
+                       (const void *)cell_pass_kernel<R, 1, 0>,    (const void *)cell_pass_kernel<R, 2, 8>,
+                       (const void *)cell_pass_kernel<R, 2, 16>,   (const void *)cell_pass_kernel<R, 2, 0>};
   for (const void *f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
@@ -632,10 +648,14 @@ cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const 
 #define VET_CELL(MODE, BC)                                                                                  \
   cell_launch<R, MODE, BC>(g, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, \
                            status, st)
-  if (mode == 0) {
+  if (mode == 0 && M_out) {
     if (g.B == 16) VET_CELL(0, 16);
     else if (g.B == 8) VET_CELL(0, 8);
     else VET_CELL(0, 0);
+  } else if (mode == 0) {
+    if (g.B == 16) VET_CELL(2, 16);
+    else if (g.B == 8) VET_CELL(2, 8);
+    else VET_CELL(2, 0);
   } else {
     if (g.B == 16) VET_CELL(1, 16);
     else if (g.B == 8) VET_CELL(1, 8);
