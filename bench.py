@@ -201,6 +201,8 @@ def run_ours(args, rank, world, local_rank):
     cell_segs, face_segs = ctx.work_counts()
     launches = ctx.launches_per_closure()
 
+    tuning = ctx.autotune(kappa, S)  # the library's own tile choice, before timing
+    cfg["tuning"] = {"face_group": tuning[0], "dir_tile": tuning[1]}
     for _ in range(args.warmup):
         ctx.closure(kappa, S, None, f)
     ctx.set_timing(True)

@@ -148,9 +148,58 @@ vet_status vet_set_timing(vet_ctx *ctx, int enable);
 vet_status vet_last_timing(vet_ctx *ctx, float ms[4]);
 
 /* Kernel launches one vet_closure call makes (its work is split into this
- * many kernels: one per wavefront level of the face pass, the cell pass and
- * the closing step). */
+ * many kernels: the boundary fill, one per wavefront level of the face pass,
+ * the cell pass and the closing step). */
 int vet_launches_per_closure(const vet_ctx *ctx);
+
+/* Performance tunables of the two passes (SURVEY-style autotuning; the paper
+ * has no counterpart -- its tracer runs on CPUs):
+ *   face_group -- directions of one octant per face-pass work item, 1..8;
+ *   dir_tile   -- directions per cell-pass staging tile, 1..8 (clamped to
+ *                 what fits twice in shared memory).
+ * 0 keeps the current value.  Results change only at rounding level (the
+ * order of the partial sums over directions). */
+vet_status vet_set_tuning(vet_ctx *ctx, int face_group, int dir_tile);
+vet_status vet_get_tuning(const vet_ctx *ctx, int *face_group, int *dir_tile);
+
+/* Time vet_closure on the given device inputs for the candidate tunings
+ * {2,4,8} x {2,4,8}, keep the fastest and report it (either out pointer may
+ * be NULL).  Allocates one f-sized scratch buffer for the duration of the
+ * call.  FP32 contexts. */
+vet_status vet_autotune(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, int *face_group,
+                        int *dir_tile, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batches of independent grids (ragged sizes, block edges and direction
+ * sets).  Each grid gets its own context (vet_create); vet_batch_closure
+ * runs one closure per grid, each on its own branch of one CUDA graph that is
+ * captured on the first call and replayed while the field pointers stay the
+ * same, so the grids' kernels run concurrently and the whole batch costs one
+ * graph launch.  FP32, one device, device pointers only.
+ * ---------------------------------------------------------------------- */
+typedef struct vet_batch vet_batch;
+
+vet_status vet_batch_create(vet_batch **out, int n, const vet_grid *grids, const vet_config *cfgs);
+vet_status vet_batch_destroy(vet_batch *batch);
+
+/* The context of grid i (directions, work counts, tuning), owned by the
+ * batch; NULL when i is out of range. */
+vet_ctx *vet_batch_context(vet_batch *batch, int i);
+
+/* Arrays of n pointers, one per grid; Ib and M_out may be NULL (or hold NULL
+ * entries).  Enqueued on `stream`; errors of the device work are reported by
+ * vet_batch_sync. */
+vet_status vet_batch_closure(vet_batch *batch, const float *const *kappa, const float *const *S,
+                             const float *const *Ib, float *const *f_out, float *const *M_out, void *stream);
+vet_status vet_batch_sync(vet_batch *batch);
+
+/* vet_autotune for the first grid of every distinct shape (cells, block edge,
+ * directions), applied to all grids of that shape. */
+vet_status vet_batch_autotune(vet_batch *batch, const float *const *kappa, const float *const *S,
+                              const float *const *Ib, void *stream);
+
+/* Message for the last failure on the batch.  Never NULL. */
+const char *vet_batch_last_error(const vet_batch *batch);
 
 /* Message for the last failure on ctx (or, when ctx is NULL, for the last
  * failure of vet_create or vet_closure_noalloc in this thread).  Never NULL. */

@@ -42,6 +42,8 @@ struct vet_ctx {
   void *d_stage = nullptr;       // staging of host-pointer arguments
   size_t stage_bytes = 0;
   long long cell_segs = 0, face_segs = 0;
+  int ob[9] = {0};                // octant ranges of the internal direction order
+  int face_group = vet::kFaceGroup;  // directions per face-pass item (tunable)
   cudaStream_t last_stream = nullptr;
   bool timing = false;
   bool timed = false;            // events of the last call were recorded
@@ -95,6 +97,29 @@ void free_ctx(vet_ctx *c) {
   delete c;
 }
 
+// Face-pass schedule for `group` directions per item (uploaded; replaces the
+// previous one).
+vet_status build_schedule(vet_ctx *c, int group) {
+  const int nb[3] = {c->dims.nbx, c->dims.nby, c->dims.nbz};
+  c->nlevels = nb[0] + nb[1] + nb[2] - 2;
+  std::vector<int> off(c->nlevels + 1, 0);
+  const long long nitems = vet::geom::build_schedule(nb, c->ob, group, nullptr, 1LL << 40, off.data());
+  std::vector<FaceItem> items((size_t)std::max<long long>(1, nitems));
+  vet::geom::build_schedule(nb, c->ob, group, items.data(), nitems, off.data());
+  FaceItem *d = nullptr;
+  cudaError_t e = cudaMalloc((void **)&d, sizeof(FaceItem) * items.size());
+  if (e) return cuda_err(c, e, "cudaMalloc(schedule)");
+  if ((e = cudaMemcpy(d, items.data(), sizeof(FaceItem) * items.size(), cudaMemcpyHostToDevice))) {
+    cudaFree(d);
+    return cuda_err(c, e, "upload schedule");
+  }
+  cudaFree(c->d_items);
+  c->d_items = d;
+  c->level_off = off;
+  c->face_group = group;
+  return VET_OK;
+}
+
 template <typename R>
 vet_status build_context(vet_ctx *c) {
   const int B = c->grid.block, N = c->N;
@@ -113,12 +138,7 @@ vet_status build_context(vet_ctx *c) {
   }
   c->cell_segs = cs_tot * c->nblk;
   c->face_segs = ns_tot * c->nblk;
-  const int nb[3] = {c->dims.nbx, c->dims.nby, c->dims.nbz};
-  c->nlevels = nb[0] + nb[1] + nb[2] - 2;
-  c->level_off.assign(c->nlevels + 1, 0);
-  const long long nitems = vet::geom::build_schedule(nb, ob, vet::kFaceGroup, nullptr, 1LL << 40, c->level_off.data());
-  std::vector<FaceItem> items((size_t)nitems);
-  vet::geom::build_schedule(nb, ob, vet::kFaceGroup, items.data(), nitems, c->level_off.data());
+  std::memcpy(c->ob, ob, sizeof ob);
   std::vector<int> cell_order(N);
   vet::geom::interleaved_order(ob, cell_order.data());
   // moment coefficients in HEALPix order
@@ -133,8 +153,6 @@ vet_status build_context(vet_ctx *c) {
   c->dims.fstride = vet::face_stride_elems<R>(B);
   const size_t face_elems = (size_t)N * c->nblk * 3 * c->dims.fstride;
   if ((e = cudaMalloc(&c->d_tpl, tpl.size()))) return cuda_err(c, e, "cudaMalloc(templates)");
-  if ((e = cudaMalloc((void **)&c->d_items, sizeof(FaceItem) * std::max<size_t>(1, items.size()))))
-    return cuda_err(c, e, "cudaMalloc(schedule)");
   if ((e = cudaMalloc(&c->d_faces, sizeof(R) * face_elems))) return cuda_err(c, e, "cudaMalloc(face intensities)");
   // the padding row and column of every stored face stay zero for good
   if ((e = cudaMemset(c->d_faces, 0, sizeof(R) * face_elems))) return cuda_err(c, e, "cudaMemset(face intensities)");
@@ -147,9 +165,8 @@ vet_status build_context(vet_ctx *c) {
   if ((e = cudaMemset(c->d_status, 0, sizeof(int)))) return cuda_err(c, e, "cudaMemset(status)");
   if ((e = cudaMemcpy(c->d_tpl, tpl.data(), tpl.size(), cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload templates");
-  if (!items.empty() &&
-      (e = cudaMemcpy(c->d_items, items.data(), sizeof(FaceItem) * items.size(), cudaMemcpyHostToDevice)))
-    return cuda_err(c, e, "upload schedule");
+  vet_status st = build_schedule(c, c->face_group);
+  if (st != VET_OK) return st;
   if ((e = cudaMalloc((void **)&c->d_cell_order, sizeof(int) * N))) return cuda_err(c, e, "cudaMalloc(order)");
   if ((e = cudaMemcpy(c->d_cell_order, cell_order.data(), sizeof(int) * N, cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload order");
@@ -293,7 +310,7 @@ vet_status run_face_pass(vet_ctx *c, const R *kappa, const R *S, const R *Ib, cu
   for (int L = 0; L < c->nlevels; ++L) {
     const int n = c->level_off[L + 1] - c->level_off[L];
     e = vet::launch_face_level<R>(c->dims, kappa, S, (const unsigned char *)c->d_tpl, c->d_items + c->level_off[L], n,
-                                  vet::kFaceGroup, (R *)c->d_faces, (const R *)c->d_bnd, c->spin, c->d_status, st);
+                                  c->face_group, (R *)c->d_faces, (const R *)c->d_bnd, c->spin, c->d_status, st);
     if (e) return cuda_err(c, e, "face pass launch");
   }
   return VET_OK;
@@ -548,8 +565,267 @@ VET_API int vet_launches_per_closure(const vet_ctx *ctx) {
   if (!ctx) return -1;
   int n = 0;
   for (int L = 0; L < ctx->nlevels; ++L) n += ctx->level_off[L + 1] > ctx->level_off[L];
-  return n + 2;
+  return n + 3;  // + boundary fill, cell pass, floor fix
 }
+
+VET_API vet_status vet_set_tuning(vet_ctx *ctx, int face_group, int dir_tile) {
+  if (!ctx) return VET_EINVAL;
+  if (face_group < 0 || face_group > vet::kMaxTune || dir_tile < 0 || dir_tile > vet::kMaxTune)
+    return set_err(ctx, VET_EINVAL, "face_group and dir_tile must be in 0..8 (0 keeps the current value)");
+  DeviceGuard dg(ctx->cfg.device);
+  if (face_group > 0 && face_group != ctx->face_group) {
+    if (vet::pass_smem_bytes(ctx->grid.block, face_group, ctx->fp64) > 232448 - 64)
+      return set_err(ctx, VET_EUNSUPPORTED, "face_group too large for this block edge's shared memory");
+    vet_status st = build_schedule(ctx, face_group);
+    if (st != VET_OK) return st;
+  }
+  if (dir_tile > 0) ctx->dims.dir_tile = vet::cell_tile_fit(ctx->grid.block, dir_tile, ctx->fp64);
+  return VET_OK;
+}
+
+VET_API vet_status vet_get_tuning(const vet_ctx *ctx, int *face_group, int *dir_tile) {
+  if (!ctx || !face_group || !dir_tile) return VET_EINVAL;
+  *face_group = ctx->face_group;
+  *dir_tile = vet::cell_tile_fit(ctx->grid.block, ctx->dims.dir_tile > 0 ? ctx->dims.dir_tile : 4, ctx->fp64);
+  return VET_OK;
+}
+
+VET_API vet_status vet_autotune(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, int *face_group,
+                                int *dir_tile, void *stream) {
+  vet_status s = check_ctx<float>(ctx, false);
+  if (s) return s;
+  if (!kappa || !S) return set_err(ctx, VET_EINVAL, "kappa and S are required");
+  DeviceGuard dg(ctx->cfg.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  float *f = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaMalloc((void **)&f, sizeof(float) * 6 * (size_t)ctx->dims.ncell);
+  if (e) return cuda_err(ctx, e, "cudaMalloc(autotune output)");
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int old_fg = ctx->face_group, old_dt = ctx->dims.dir_tile;
+  const bool old_timing = ctx->timing;
+  ctx->timing = false;
+  float best = 1e30f;
+  int best_fg = old_fg, best_dt = old_dt;
+  const int cand[3] = {2, 4, 8};
+  for (int i = 0; i < 3 && s == VET_OK; ++i) {
+    for (int j = 0; j < 3 && s == VET_OK; ++j) {
+      if (vet_set_tuning(ctx, cand[i], cand[j]) != VET_OK) continue;
+      if (ctx->dims.dir_tile != cand[j]) continue;  // did not fit
+      float t = 1e30f;
+      for (int rep = 0; rep < 3 && s == VET_OK; ++rep) {  // first run warms up
+        cudaEventRecord(a, st);
+        s = do_closure<float>(ctx, kappa, S, Ib, f, nullptr, st, false);
+        cudaEventRecord(b, st);
+        if (s == VET_OK && (e = cudaEventSynchronize(b))) s = cuda_err(ctx, e, "autotune run");
+        float ms = 0.f;
+        if (s == VET_OK && rep > 0 && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) t = std::min(t, ms);
+      }
+      if (s == VET_OK && t < best) {
+        best = t;
+        best_fg = cand[i];
+        best_dt = cand[j];
+      }
+    }
+  }
+  ctx->timing = old_timing;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(f);
+  if (s != VET_OK) {
+    vet_set_tuning(ctx, old_fg, old_dt > 0 ? old_dt : 4);
+    return s;
+  }
+  s = vet_set_tuning(ctx, best_fg, best_dt);
+  if (s == VET_OK && face_group) *face_group = best_fg;
+  if (s == VET_OK && dir_tile) *dir_tile = best_dt;
+  return s;
+}
+
+// ------------------------------------------------------------- batches
+struct vet_batch {
+  int n = 0;
+  int device = 0;
+  std::vector<vet_ctx *> ctx;
+  std::vector<cudaStream_t> branch;   // one capture stream per grid
+  std::vector<cudaEvent_t> joined;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t forked = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void *> key;      // pointers the graph was captured with
+  std::string err;
+};
+
+namespace {
+
+vet_status batch_err(vet_batch *b, vet_status st, const std::string &msg) {
+  b->err = msg;
+  return st;
+}
+
+void free_batch(vet_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto s : b->branch) cudaStreamDestroy(s);
+  for (auto e : b->joined) cudaEventDestroy(e);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->forked) cudaEventDestroy(b->forked);
+  for (auto c : b->ctx) free_ctx(c);
+  delete b;
+}
+
+}  // namespace
+
+VET_API vet_status vet_batch_create(vet_batch **out, int n, const vet_grid *grids, const vet_config *cfgs) {
+  if (!out) return set_err(nullptr, VET_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !grids || !cfgs) return set_err(nullptr, VET_EINVAL, "n >= 1 grids and configs are required");
+  vet_batch *b = new (std::nothrow) vet_batch;
+  if (!b) return set_err(nullptr, VET_ENOMEM, "host allocation failed");
+  b->n = n;
+  b->device = cfgs[0].device;
+  for (int i = 0; i < n; ++i) {
+    if (cfgs[i].precision != VET_FP32 || cfgs[i].device != b->device) {
+      free_batch(b);
+      return set_err(nullptr, VET_EINVAL, "a batch holds FP32 grids on one device");
+    }
+    vet_ctx *c = nullptr;
+    vet_status st = vet_create(&c, &grids[i], &cfgs[i]);
+    if (st != VET_OK) {
+      g_create_err = "grid " + std::to_string(i) + ": " + g_create_err;
+      free_batch(b);
+      return st;
+    }
+    b->ctx.push_back(c);
+  }
+  DeviceGuard dg(b->device);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming);
+  for (int i = 0; i < n && !e; ++i) {
+    cudaStream_t s;
+    cudaEvent_t ev;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking))) break;
+    b->branch.push_back(s);
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) break;
+    b->joined.push_back(ev);
+  }
+  if (e) {
+    free_batch(b);
+    return set_err(nullptr, VET_ECUDA, std::string("batch streams: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return VET_OK;
+}
+
+VET_API vet_status vet_batch_destroy(vet_batch *b) {
+  if (!b) return VET_OK;
+  DeviceGuard dg(b->device);
+  free_batch(b);
+  return VET_OK;
+}
+
+VET_API vet_ctx *vet_batch_context(vet_batch *b, int i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->ctx[i];
+}
+
+VET_API vet_status vet_batch_closure(vet_batch *b, const float *const *kappa, const float *const *S,
+                                     const float *const *Ib, float *const *f_out, float *const *M_out, void *stream) {
+  if (!b || !kappa || !S || !f_out) return VET_EINVAL;
+  std::vector<const void *> key;
+  for (int i = 0; i < b->n; ++i) {
+    if (!kappa[i] || !S[i] || !f_out[i]) return batch_err(b, VET_EINVAL, "missing field pointer");
+    if (!is_device_ptr(kappa[i]) || !is_device_ptr(S[i]) || !is_device_ptr(f_out[i]) ||
+        (Ib && Ib[i] && !is_device_ptr(Ib[i])) || (M_out && M_out[i] && !is_device_ptr(M_out[i])))
+      return batch_err(b, VET_EINVAL, "batch field pointers must be device memory");
+    key.insert(key.end(), {kappa[i], S[i], Ib ? Ib[i] : nullptr, f_out[i], M_out ? M_out[i] : nullptr});
+  }
+  DeviceGuard dg(b->device);
+  if (!b->exec || key != b->key) {
+    // capture one closure per grid, each on its own branch of the graph
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+    if (e) return batch_err(b, VET_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    vet_status st = VET_OK;
+    e = cudaEventRecord(b->forked, b->origin);
+    for (int i = 0; i < b->n && !e && st == VET_OK; ++i) {
+      if ((e = cudaStreamWaitEvent(b->branch[i], b->forked, 0))) break;
+      vet_ctx *c = b->ctx[i];
+      const bool timing = c->timing;
+      c->timing = false;
+      st = do_closure<float>(c, kappa[i], S[i], Ib ? Ib[i] : nullptr, f_out[i], M_out ? M_out[i] : nullptr,
+                             b->branch[i], false);
+      c->timing = timing;
+      if (st != VET_OK) b->err = "grid " + std::to_string(i) + ": " + c->err;
+      if (!e) e = cudaEventRecord(b->joined[i], b->branch[i]);
+      if (!e) e = cudaStreamWaitEvent(b->origin, b->joined[i], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->origin, &graph);
+    if (st != VET_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e || e2) {
+      if (graph) cudaGraphDestroy(graph);
+      return batch_err(b, VET_ECUDA, std::string("capture: ") + cudaGetErrorString(e ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e) {
+      b->exec = nullptr;
+      return batch_err(b, VET_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    b->key = key;
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e) return batch_err(b, VET_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  for (auto c : b->ctx) c->last_stream = (cudaStream_t)stream;
+  return VET_OK;
+}
+
+VET_API vet_status vet_batch_sync(vet_batch *b) {
+  if (!b) return VET_EINVAL;
+  for (int i = 0; i < b->n; ++i) {
+    vet_status st = vet_sync(b->ctx[i]);
+    if (st != VET_OK) return batch_err(b, st, "grid " + std::to_string(i) + ": " + b->ctx[i]->err);
+  }
+  return VET_OK;
+}
+
+VET_API vet_status vet_batch_autotune(vet_batch *b, const float *const *kappa, const float *const *S,
+                                      const float *const *Ib, void *stream) {
+  if (!b || !kappa || !S) return VET_EINVAL;
+  // one tuning per distinct grid shape, applied to every grid of that shape
+  for (int i = 0; i < b->n; ++i) {
+    const vet_ctx *ci = b->ctx[i];
+    int j = 0;
+    for (; j < i; ++j) {
+      const vet_ctx *cj = b->ctx[j];
+      if (cj->grid.nx == ci->grid.nx && cj->grid.ny == ci->grid.ny && cj->grid.nz == ci->grid.nz &&
+          cj->grid.block == ci->grid.block && cj->N == ci->N)
+        break;
+    }
+    vet_status st;
+    if (j < i) {
+      st = vet_set_tuning(b->ctx[i], b->ctx[j]->face_group, b->ctx[j]->dims.dir_tile);
+    } else {
+      st = vet_autotune(b->ctx[i], kappa[i], S[i], Ib ? Ib[i] : nullptr, nullptr, nullptr, stream);
+    }
+    if (st != VET_OK) return batch_err(b, st, "grid " + std::to_string(i) + ": " + b->ctx[i]->err);
+  }
+  if (b->exec) {  // tunings changed the launches: capture again on the next call
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return VET_OK;
+}
+
+VET_API const char *vet_batch_last_error(const vet_batch *b) { return b ? b->err.c_str() : ""; }
 
 VET_API const char *vet_last_error(const vet_ctx *ctx) {
   if (!ctx) return g_create_err.c_str();

@@ -89,6 +89,7 @@ struct GridDims {
   int fstride;        // elements per stored face: (B+2)^2 rounded up to 16 bytes
   int ndir;           // directions
   long long ncell;    // nx*ny*nz
+  int dir_tile;       // directions per cell-pass tile (0: default)
 };
 
 // Shared-memory kappa/S tiles of a block.  Face pass: cell (x, y, z) at
@@ -158,11 +159,15 @@ cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef,
 // Dynamic shared memory of a CTA staging `dirs` directions.
 size_t pass_smem_bytes(int B, int dirs, bool fp64);
 
+// Largest cell-pass direction tile (<= want) whose two buffers fit.
+int cell_tile_fit(int B, int want, bool fp64);
+
 // Bytes of one staged direction (template + three faces).
 size_t face_slot_bytes(int B, bool fp64);
 
-// Directions per face-pass item.
+// Directions per face-pass item (default; a context may be tuned to 1..8).
 constexpr int kFaceGroup = 4;
+constexpr int kMaxTune = 8;
 
 // Per-device kernel attributes; call with the context's device current.
 cudaError_t prepare_kernels();

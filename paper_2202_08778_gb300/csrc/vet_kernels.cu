@@ -260,8 +260,8 @@ constexpr int kDirTile = 4;   // directions per cell-pass tile (two tiles in fli
 constexpr size_t kSmemMax = 232448 - 64;  // opt-in limit less the static mbarriers
 
 template <typename R>
-int cell_dir_tile(int B) {
-  int dt = kDirTile;
+int cell_dir_tile(int B, int want) {
+  int dt = want > 0 ? want : kDirTile;
   while (dt > 1 && smem_bytes<R>(B, 2 * dt) > kSmemMax) --dt;
   return dt;
 }
@@ -607,7 +607,7 @@ void cell_launch(const GridDims &g, const R *kappa, const R *S, const unsigned c
   const int cpc = g.B * g.B * g.B / parts;
   const int threads = (cpc + 31) / 32 * 32;
   const int nblk = g.nbx * g.nby * g.nbz;
-  const int dt = cell_dir_tile<R>(g.B);
+  const int dt = cell_dir_tile<R>(g.B, g.dir_tile);
   cell_pass_kernel<R, MODE, BC><<<nblk * parts, threads, smem_bytes<R>(g.B, 2 * dt), st>>>(
       g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, status);
 }
@@ -693,6 +693,10 @@ cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef,
 
 size_t pass_smem_bytes(int B, int dirs, bool fp64) {
   return fp64 ? smem_bytes<double>(B, dirs) : smem_bytes<float>(B, dirs);
+}
+
+int cell_tile_fit(int B, int want, bool fp64) {
+  return fp64 ? cell_dir_tile<double>(B, want) : cell_dir_tile<float>(B, want);
 }
 
 size_t face_slot_bytes(int B, bool fp64) { return fp64 ? slot_bytes<double>(B) : slot_bytes<float>(B); }

@@ -28,6 +28,8 @@ EXPORTS = (
     "vet_create", "vet_destroy", "vet_num_directions", "vet_directions", "vet_trace", "vet_moments",
     "vet_closure", "vet_trace_f64", "vet_moments_f64", "vet_closure_f64", "vet_sync", "vet_work_counts",
     "vet_set_timing", "vet_last_timing", "vet_launches_per_closure", "vet_last_error", "vet_closure_noalloc",
+    "vet_set_tuning", "vet_get_tuning", "vet_autotune", "vet_batch_create", "vet_batch_destroy", "vet_batch_context",
+    "vet_batch_closure", "vet_batch_sync", "vet_batch_autotune", "vet_batch_last_error",
 )
 
 
@@ -86,10 +88,24 @@ def load(build_if_missing: bool = True):
         lib.vet_launches_per_closure.argtypes = [vp]
         lib.vet_launches_per_closure.restype = i
         lib.vet_closure_noalloc.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Config), vp, vp, vp, vp, vp, vp]
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.vet_set_tuning.argtypes = [vp, i, i]
+        lib.vet_get_tuning.argtypes = [vp, ip, ip]
+        lib.vet_autotune.argtypes = [vp, vp, vp, vp, ip, ip, vp]
+        lib.vet_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(_Grid), ctypes.POINTER(_Config)]
+        lib.vet_batch_destroy.argtypes = [vp]
+        lib.vet_batch_context.argtypes = [vp, i]
+        lib.vet_batch_context.restype = vp
+        lib.vet_batch_closure.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.vet_batch_sync.argtypes = [vp]
+        lib.vet_batch_autotune.argtypes = [vp, vp, vp, vp, vp]
+        lib.vet_batch_last_error.argtypes = [vp]
+        lib.vet_batch_last_error.restype = ctypes.c_char_p
         lib.vet_last_error.argtypes = [vp]
         lib.vet_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("vet_num_directions", "vet_last_error", "vet_launches_per_closure"):
+            if name not in ("vet_num_directions", "vet_last_error", "vet_launches_per_closure", "vet_batch_context",
+                            "vet_batch_last_error"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -220,6 +236,23 @@ class Context:
     def sync(self):
         self._check(self._lib.vet_sync(self._h))
 
+    def set_tuning(self, face_group: int = 0, dir_tile: int = 0):
+        self._check(self._lib.vet_set_tuning(self._h, int(face_group), int(dir_tile)))
+
+    def tuning(self):
+        fg, dt = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.vet_get_tuning(self._h, ctypes.byref(fg), ctypes.byref(dt)))
+        return fg.value, dt.value
+
+    def autotune(self, kappa, S, Ib=None, stream=None):
+        """Time the candidate tunings on these device inputs; keep the fastest."""
+        nc = self.ncell
+        fg, dt = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.vet_autotune(self._h, _ptr(kappa, np.float32, nc, "kappa"), _ptr(S, np.float32, nc, "S"),
+                                           _ptr(Ib, np.float32, 6 * self.N, "Ib"), ctypes.byref(fg),
+                                           ctypes.byref(dt), _stream(stream)))
+        return fg.value, dt.value
+
 
 def closure_noalloc(shape, block: int, h: float, nside: int, kappa, S, Ib, f_out, M_out=None,
                     rot_q=(1.0, 0.0, 0.0, 0.0), device: int = 0, spin_limit: int = 0, stream=None):
@@ -240,3 +273,86 @@ def closure_noalloc(shape, block: int, h: float, nside: int, kappa, S, Ib, f_out
     if st != VET_OK:
         raise VetError(st, lib.vet_last_error(None).decode())
     return f_out
+
+
+class _Member(Context):
+    """A grid of a Batch: a view of a context the batch owns."""
+
+    def __init__(self, lib, handle, shape):
+        self._lib = lib
+        self._h = ctypes.c_void_p(handle)
+        self.shape = tuple(int(v) for v in shape)
+        self.ncell = int(np.prod(self.shape))
+        self.precision = VET_FP32
+        self.dtype = np.float32
+        self.N = lib.vet_num_directions(self._h)
+
+    def close(self):  # owned by the batch
+        self._h = None
+
+
+class Batch:
+    """vet_batch: independent grids whose closures run as one CUDA graph
+    (one branch per grid).  problems: list of (shape, block, h, nside, rot_q)."""
+
+    def __init__(self, problems, device: int = 0, spin_limit: int = 0):
+        self._lib = load()
+        n = len(problems)
+        grids = (_Grid * n)()
+        cfgs = (_Config * n)()
+        for i, (shape, block, h, nside, q) in enumerate(problems):
+            nz, ny, nx = shape
+            grids[i] = _Grid(int(nx), int(ny), int(nz), int(block), float(h))
+            cfgs[i] = _Config(int(nside), (ctypes.c_double * 4)(*[float(v) for v in q]), VET_FP32, int(device),
+                              int(spin_limit))
+        h_ = ctypes.c_void_p()
+        st = self._lib.vet_batch_create(ctypes.byref(h_), n, grids, cfgs)
+        if st != VET_OK:
+            raise VetError(st, self._lib.vet_last_error(None).decode())
+        self._h = h_
+        self.n = n
+        self.members = [_Member(self._lib, self._lib.vet_batch_context(self._h, i), problems[i][0]) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m.close()
+            self._lib.vet_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != VET_OK:
+            raise VetError(st, self._lib.vet_batch_last_error(self._h).decode())
+
+    def _arr(self, xs, sizes, name, allow_none=False):
+        if xs is None:
+            return None
+        arr = (ctypes.c_void_p * self.n)()
+        for i, (x, n) in enumerate(zip(xs, sizes)):
+            if x is None and allow_none:
+                arr[i] = None
+            else:
+                arr[i] = _ptr(x, np.float32, n, f"{name}[{i}]")
+        return arr
+
+    def closure(self, kappa, S, Ib, f_out, M_out=None, stream=None):
+        nc = [m.ncell for m in self.members]
+        self._check(self._lib.vet_batch_closure(
+            self._h, self._arr(kappa, nc, "kappa"), self._arr(S, nc, "S"),
+            self._arr(Ib, [6 * m.N for m in self.members], "Ib", True), self._arr(f_out, [6 * c for c in nc], "f_out"),
+            self._arr(M_out, [10 * c for c in nc], "M_out", True), _stream(stream)))
+
+    def autotune(self, kappa, S, Ib=None, stream=None):
+        nc = [m.ncell for m in self.members]
+        self._check(self._lib.vet_batch_autotune(self._h, self._arr(kappa, nc, "kappa"), self._arr(S, nc, "S"),
+                                                 self._arr(Ib, [6 * m.N for m in self.members], "Ib", True),
+                                                 _stream(stream)))
+
+    def sync(self):
+        self._check(self._lib.vet_batch_sync(self._h))

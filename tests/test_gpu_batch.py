@@ -1,0 +1,91 @@
+"""Batched closures of independent ragged grids (one CUDA graph, one branch
+per grid): identical to the grids' own closures, repeatable on graph replay,
+within tolerance of the FP64 oracle, and unchanged (to rounding) by the
+autotuner's choice of tiles."""
+import numpy as np
+import pytest
+
+from gpu_common import f_error, moment_errors
+from paper_2202_08778_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2202_08778_gb300 import vet  # noqa: E402
+
+
+def _batch(problems):
+    specs = [(p["kappa"].shape, p["B"], p["h"], p["nside"], p["q"]) for p in problems]
+    k = [torch.from_numpy(p["kappa"].astype(np.float32)).cuda() for p in problems]
+    s = [torch.from_numpy(p["S"].astype(np.float32)).cuda() for p in problems]
+    return specs, k, s
+
+
+def test_small_ragged_batch_matches_single_grids_and_oracle(ora):
+    problems = synth.batched_problems(n_grids=6, seed0=100, edges=(16, 32, 48), blocks=(8, 16), nsides=(2, 4))
+    specs, k, s = _batch(problems)
+    batch = vet.Batch(specs)
+    f = [torch.empty(6 * x.numel(), device="cuda") for x in k]
+    M = [torch.empty(10 * x.numel(), device="cuda") for x in k]
+    batch.closure(k, s, None, f, M)
+    batch.sync()
+    first = [x.clone() for x in f]
+    batch.closure(k, s, None, f, M)  # graph replay
+    batch.sync()
+    for i, p in enumerate(problems):
+        assert torch.equal(f[i], first[i])
+        ctx = vet.Context(*specs[i])
+        fr = torch.empty_like(f[i])
+        Mr = torch.empty_like(M[i])
+        ctx.closure(k[i], s[i], None, fr, Mr)
+        ctx.sync()
+        assert torch.equal(fr, f[i]) and torch.equal(Mr, M[i])
+    small = sorted(range(len(problems)), key=lambda i: problems[i]["kappa"].size)[:2]
+    for i in small:
+        p = problems[i]
+        kk = p["kappa"].astype(np.float32).astype(np.float64)
+        ss = p["S"].astype(np.float32).astype(np.float64)
+        f_ref, M_ref, _, _ = ora.vet_closure(kk, ss, batch.members[i].directions(), p["B"], p["h"])
+        eE, eFP = moment_errors(M[i].cpu().numpy(), M_ref)
+        assert eE < 1e-5 and eFP < 1e-5
+        assert f_error(f[i].cpu().numpy(), f_ref, M_ref) < 1e-6
+
+
+def test_autotune_keeps_results_and_picks_valid_tiles():
+    problems = synth.batched_problems(n_grids=4, seed0=120, edges=(32, 48), blocks=(8, 16), nsides=(2, 4))
+    specs, k, s = _batch(problems)
+    batch = vet.Batch(specs)
+    f0 = [torch.empty(6 * x.numel(), device="cuda") for x in k]
+    batch.closure(k, s, None, f0)
+    batch.sync()
+    batch.autotune(k, s)
+    for m in batch.members:
+        fg, dt = m.tuning()
+        assert fg in (2, 4, 8) and dt in (1, 2, 3, 4, 5, 6, 7, 8)
+    f1 = [torch.empty_like(x) for x in f0]
+    batch.closure(k, s, None, f1)
+    batch.sync()
+    for a, b in zip(f0, f1):
+        assert (a - b).abs().max().item() < 1e-6
+
+
+def test_config4_batch_of_64_ragged_grids():
+    """The 64-grid batch (edges 32..96, 8^3 or 16^3 blocks, 48 or 192
+    directions): every grid equals its own closure."""
+    problems = synth.batched_problems(n_grids=64, seed0=100)
+    specs, k, s = _batch(problems)
+    batch = vet.Batch(specs)
+    f = [torch.empty(6 * x.numel(), device="cuda") for x in k]
+    batch.closure(k, s, None, f)
+    batch.sync()
+    for i in (0, 17, 42, 63):
+        ctx = vet.Context(*specs[i])
+        fr = torch.empty_like(f[i])
+        ctx.closure(k[i], s[i], None, fr)
+        ctx.sync()
+        assert torch.equal(fr, f[i])
+        fi = f[i].view(6, -1)
+        assert (fi[0] + fi[1] + fi[2] - 1).abs().max().item() < 1e-6
