@@ -152,8 +152,8 @@ vet_status vet_last_timing(vet_ctx *ctx, float ms[4]);
  * the cell pass and the closing step). */
 int vet_launches_per_closure(const vet_ctx *ctx);
 
-/* Performance tunables of the two passes (SURVEY-style autotuning; the paper
- * has no counterpart -- its tracer runs on CPUs):
+/* Performance tunables of the two passes (autotuned; the paper has no
+ * counterpart -- its tracer runs on CPUs):
  *   face_group -- directions of one octant per face-pass work item, 1..8;
  *   dir_tile   -- directions per cell-pass staging tile, 1..8 (clamped to
  *                 what fits twice in shared memory).
@@ -200,6 +200,104 @@ vet_status vet_batch_autotune(vet_batch *batch, const float *const *kappa, const
 
 /* Message for the last failure on the batch.  Never NULL. */
 const char *vet_batch_last_error(const vet_batch *batch);
+
+/* ------------------------------------------------------------------------
+ * Learned closure (not in the paper, whose closures are the exact VET, M1
+ * and Eddington, Sec. 2.2.5 and App. A): a small 3D convolutional network
+ * predicts f from local features; the exact ray tracer above is its fallback
+ * and the judge of its error.
+ *
+ * Features per cell (6): 1 (validity; the zero padding at the domain edge
+ * reads 0), log10(kappa h), log10 S and log10 E each minus its mean over the
+ * volume (f does not change when S, and with it I and E, is scaled), and the
+ * mean and population standard deviation of log10(kappa h) over the cell's
+ * block.  Arguments of log10 are clamped below at 1e-30.
+ * Network: four 3x3x3 convolutions with zero padding, 6 -> C -> C -> C -> 7
+ * channels (C = 32), SiLU z/(1+exp(-z)) after the first three; BF16 weights
+ * and activations, FP32 accumulation, FP32 master weights.  Outputs 0..5 are
+ * a correction D (xx, yy, zz, xy, xz, yz) to I/3 with the trace projected
+ * out: f_ii = 1/3 + D_ii - tr(D)/3, f_ij = D_ij.  Output 6 is the log of the
+ * predicted max_ij |f - f_exact|.
+ * Loss: mean over cells and components of (f - f_ref)^2 plus
+ * lam * mean over cells of (o6 - log(max_ij |f - f_ref| + 1e-4))^2, the
+ * target of o6 held constant.
+ * Indicator: r = max(-lambda_min(f), lambda_max(f) - 1, exp(o6), 0); blocks
+ * holding a cell with r > threshold are recomputed by the exact closure.
+ *
+ * Parameters cross the ABI as one FP32 host array: for each layer in order,
+ * W[27][C_out][C_in] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1), the input cell at
+ * offset (dx, dy, dz)) then b[C_out], with the real channel counts above.
+ * All field pointers of the model calls are device memory; work is enqueued
+ * on `stream`.  A model is not thread-safe.
+ * ---------------------------------------------------------------------- */
+typedef struct vet_model vet_model;
+
+/* Create a model on `device` with `channels` hidden channels (32 is the
+ * only value this build supports).  Weights start at zero: call
+ * vet_model_set_params. */
+vet_status vet_model_create(vet_model **out, int channels, int device);
+vet_status vet_model_destroy(vet_model *model);
+
+/* Number of parameters in the host layout (66631 for 32 channels), or -1. */
+long long vet_model_num_params(const vet_model *model);
+
+/* Host FP32 parameters in / out.  set_params also resets the optimiser
+ * (moments and step count) and synchronises the device. */
+vet_status vet_model_set_params(vet_model *model, const float *params);
+vet_status vet_model_get_params(vet_model *model, float *params);
+
+/* Host FP32 copy of the gradients of the last vet_model_backward (same
+ * layout as the parameters). */
+vet_status vet_model_get_grads(vet_model *model, float *grads);
+
+/* Features of `nvol` volumes of the grid (each [nz][ny][nx], stacked) into
+ * the model's workspace: kappa, S, E are [nvol][nz][ny][nx]; grid->block is
+ * the block of the block statistics and must divide every extent.
+ * feat_out (optional, [nvol][6][cells]) receives the FP32 features before
+ * their rounding to BF16. */
+vet_status vet_model_features(vet_model *model, const vet_grid *grid, int nvol, const float *kappa,
+                              const float *S, const float *E, float *feat_out, void *stream);
+
+/* Network forward pass on the current features, keeping what the backward
+ * pass needs.  o_out (optional, [nvol][7][cells] FP32) receives the raw
+ * outputs. */
+vet_status vet_model_forward(vet_model *model, float *o_out, void *stream);
+
+/* Loss of the last forward pass against f_ref [nvol][6][cells] and the
+ * gradients of all parameters.  mask (optional, [nvol][cells] bytes) selects
+ * the cells that count (nonzero).  loss_out (optional) is a DEVICE double. */
+vet_status vet_model_backward(vet_model *model, const float *f_ref, const uint8_t *mask, float lam,
+                              double *loss_out, void *stream);
+
+/* One AdamW step (decoupled weight decay, applied to every parameter) with
+ * the gradients of the last backward pass. */
+vet_status vet_model_step(vet_model *model, float lr, float beta1, float beta2, float eps, float weight_decay,
+                          void *stream);
+
+/* Learned closure of one grid with the exact closure as fallback: features
+ * from (kappa, S, E) (E is the caller's radiation energy density, e.g. from
+ * its moment solve), network, indicator, then vet_closure's computation on
+ * every block whose indicator exceeds `threshold`.  ctx (FP32) supplies the
+ * grid, directions and tracer; f_out [6][cells].  block_flags_out (optional,
+ * device [blocks] uint32, blocks x-fastest) receives 1 for the recomputed
+ * blocks; *n_fallback_out (optional, host) their number.  The call
+ * synchronises `stream` once (to size the fallback); device-side timeouts of
+ * the fallback are reported by vet_sync(ctx). */
+vet_status vet_closure_learned(vet_ctx *ctx, vet_model *model, const float *kappa, const float *S,
+                               const float *E, const float *Ib, float threshold, float *f_out,
+                               uint32_t *block_flags_out, int *n_fallback_out, void *stream);
+
+/* Device time of the last vet_closure_learned, in milliseconds: ms[0] the
+ * network (features, convolutions, indicator and block list), ms[1] the
+ * fallback (exact closure on the flagged blocks), ms[2] the whole call. */
+vet_status vet_model_last_timing(vet_model *model, float ms[3]);
+
+/* Individual indicator values of the last vet_closure_learned call's grid:
+ * r_out [cells] FP32, device.  For inspection. */
+vet_status vet_model_last_indicator(vet_model *model, float *r_out, void *stream);
+
+/* Message for the last failure on the model.  Never NULL. */
+const char *vet_model_last_error(const vet_model *model);
 
 /* Message for the last failure on ctx (or, when ctx is NULL, for the last
  * failure of vet_create or vet_closure_noalloc in this thread).  Never NULL. */

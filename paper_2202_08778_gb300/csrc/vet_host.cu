@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "vet.h"
+#include "vet_bridge.h"
 #include "vet_geometry.h"
 #include "vet_internal.h"
 
@@ -409,6 +410,36 @@ vet_status do_closure(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *f_
 }  // namespace
 
 void vet::set_thread_error(const char *msg) { g_create_err = msg; }
+
+vet::CtxInfo vet::ctx_info(const vet_ctx *c) {
+  CtxInfo i{};
+  i.grid = c->grid;
+  i.ndir = c->N;
+  i.nblk = c->nblk;
+  i.fp64 = c->fp64;
+  i.device = c->cfg.device;
+  return i;
+}
+
+vet_status vet::ctx_fail(vet_ctx *c, vet_status st, const char *msg) { return set_err(c, st, msg); }
+
+vet_status vet::exact_on_blocks(vet_ctx *c, const float *kappa, const float *S, const float *Ib, const int *d_list,
+                                int nlist, float *f_out, cudaStream_t st) {
+  if (!c || c->fp64) return set_err(c, VET_EINVAL, "the learned closure needs an FP32 context");
+  if (nlist <= 0) return VET_OK;
+  cudaError_t e = cudaMemsetAsync(c->d_emax, 0, 8, st);
+  if (e) return cuda_err(c, e, "cudaMemsetAsync");
+  vet_status s = run_face_pass<float>(c, kappa, S, Ib, st);
+  if (s) return s;
+  e = vet::launch_cell_pass<float>(c->dims, 0, kappa, S, (const unsigned char *)c->d_tpl, c->d_cell_order,
+                                   (const float *)c->d_faces, (const float *)c->d_bnd, nullptr, nullptr,
+                                   (float *)c->d_E, f_out, c->d_emax, c->spin, c->d_status, st, d_list, nlist);
+  if (e) return cuda_err(c, e, "cell pass launch");
+  e = vet::launch_floor_fix_blocks<float>(c->dims, d_list, nlist, (const float *)c->d_E, c->d_emax, 1e-30, f_out, st);
+  if (e) return cuda_err(c, e, "floor launch");
+  c->last_stream = st;
+  return VET_OK;
+}
 
 VET_API vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_config *cfg) {
   if (!out) return set_err(nullptr, VET_EINVAL, "out is NULL");

@@ -138,11 +138,18 @@ cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, con
                               long long spin, int *status, cudaStream_t st);
 
 // mode 0: moments + f (+ E for the floor rule); mode 1: write I_out.  The
-// directions are visited in cell_order.
+// directions are visited in cell_order.  With a block_list (device, nlist
+// block indices) only the cells of those blocks are computed.
 template <typename R>
 cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const unsigned char *tpl,
                              const int *cell_order, const R *faces, const R *bnd, R *I_out, R *M_out, R *E_out,
-                             R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st);
+                             R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st,
+                             const int *block_list = nullptr, int nlist = 0);
+
+// The floor rule on the cells of the listed blocks.
+template <typename R>
+cudaError_t launch_floor_fix_blocks(const GridDims &g, const int *block_list, int nlist, const R *E,
+                                    const void *emax_bits, double floor_rel, R *f_out, cudaStream_t st);
 
 // bnd[face][d] <- constant Ib[face][ext(d)] (or 0 when Ib is NULL).
 template <typename R>

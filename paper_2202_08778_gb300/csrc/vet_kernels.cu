@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kCellThreads, 2)
                      const unsigned char *__restrict__ tpl_g, const int *__restrict__ order,
                      const R *__restrict__ faces, const R *__restrict__ bnd, R *__restrict__ I_out,
                      R *__restrict__ M_out, R *__restrict__ E_out, R *__restrict__ f_out, void *emax_bits,
-                     long long spin_limit, int *status) {
+                     long long spin_limit, int *status, const int *__restrict__ block_list) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[2], empty[2];
   const int B = BC ? BC : g.B;
@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(kCellThreads, 2)
   const size_t sb = slot_bytes<R>(B);
   vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
   unsigned char *buf0 = smem + align16(sizeof(vec2_t<R>) * (size_t)ts.elems);
-  const int blk = blockIdx.x / parts, part = blockIdx.x - blk * parts;
+  const int item = blockIdx.x / parts, part = blockIdx.x - item * parts;
+  const int blk = block_list ? block_list[item] : item;
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
   const int cpc = B3 / parts;  // cells of this CTA
   const int nwarps = blockDim.x >> 5;
@@ -562,6 +563,21 @@ __global__ void floor_fix_kernel(long long ncell, const R *__restrict__ E, const
 }
 
 // M[m][c] = sum_k I[k][c] coef[k][m] with coef[k] = w_k (1, n, n n).
+// The same rule on the cells of the listed blocks only.
+template <typename R>
+__global__ void floor_fix_blocks_kernel(const GridDims g, const int *__restrict__ block_list, const R *__restrict__ E,
+                                        const void *__restrict__ emax_bits, double floor_rel, R *__restrict__ f) {
+  const R floor = R(floor_rel) * load_max<R>(emax_bits);
+  const int B = g.B, blk = block_list[blockIdx.x];
+  const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
+  for (int i = threadIdx.x; i < B * B * B; i += blockDim.x) {
+    const long long c = ((long long)(bz * B + i / (B * B)) * g.ny + (by * B + (i / B) % B)) * g.nx + (bx * B + i % B);
+    if (!(E[c] > floor)) {
+      for (int m = 0; m < 6; ++m) f[m * g.ncell + c] = m < 3 ? R(1) / R(3) : R(0);
+    }
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) moments_kernel(long long ncell, int ndir, const R *__restrict__ I,
                                                       const R *__restrict__ coef, R *__restrict__ M) {
@@ -602,14 +618,15 @@ void face_launch(const GridDims &g, const R *kappa, const R *S, const unsigned c
 template <typename R, int MODE, int BC>
 void cell_launch(const GridDims &g, const R *kappa, const R *S, const unsigned char *tpl, const int *order,
                  const R *faces, const R *bnd, R *I_out, R *M_out, R *E_out, R *f_out, void *emax_bits,
-                 long long spin, int *status, cudaStream_t st) {
+                 long long spin, int *status, const int *block_list, int nlist, cudaStream_t st) {
   const int parts = cell_parts(g.B);
   const int cpc = g.B * g.B * g.B / parts;
   const int threads = (cpc + 31) / 32 * 32;
-  const int nblk = g.nbx * g.nby * g.nbz;
+  const int nblk = block_list ? nlist : g.nbx * g.nby * g.nbz;
   const int dt = cell_dir_tile<R>(g.B, g.dir_tile);
   cell_pass_kernel<R, MODE, BC><<<nblk * parts, threads, smem_bytes<R>(g.B, 2 * dt), st>>>(
-      g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, status);
+      g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, status,
+      block_list);
 }
 
 template <typename R>
@@ -644,10 +661,12 @@ cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, con
 template <typename R>
 cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const unsigned char *tpl,
                              const int *order, const R *faces, const R *bnd, R *I_out, R *M_out, R *E_out,
-                             R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st) {
+                             R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st,
+                             const int *block_list, int nlist) {
+  if (block_list && nlist <= 0) return cudaSuccess;
 #define VET_CELL(MODE, BC)                                                                                  \
   cell_launch<R, MODE, BC>(g, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, \
-                           status, st)
+                           status, block_list, nlist, st)
   if (mode == 0 && M_out) {
     if (g.B == 16) VET_CELL(0, 16);
     else if (g.B == 8) VET_CELL(0, 8);
@@ -679,6 +698,14 @@ cudaError_t launch_floor_fix(long long ncell, const R *E, long long, const void 
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   floor_fix_kernel<R><<<(int)blocks, threads, 0, st>>>(ncell, E, emax_bits, floor_rel, f_out);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_floor_fix_blocks(const GridDims &g, const int *block_list, int nlist, const R *E,
+                                    const void *emax_bits, double floor_rel, R *f_out, cudaStream_t st) {
+  if (nlist <= 0) return cudaSuccess;
+  floor_fix_blocks_kernel<R><<<nlist, 256, 0, st>>>(g, block_list, E, emax_bits, floor_rel, f_out);
   return cudaGetLastError();
 }
 
@@ -715,7 +742,9 @@ cudaError_t prepare_kernels() {
                                             cudaStream_t);                                                   \
   template cudaError_t launch_cell_pass<R>(const GridDims &, int, const R *, const R *, const unsigned char *, \
                                            const int *, const R *, const R *, R *, R *, R *, R *, void *,    \
-                                           long long, int *, cudaStream_t);                                  \
+                                           long long, int *, cudaStream_t, const int *, int);                \
+  template cudaError_t launch_floor_fix_blocks<R>(const GridDims &, const int *, int, const R *, const void *, \
+                                                  double, R *, cudaStream_t);                                \
   template cudaError_t launch_fill_boundary<R>(const GridDims &, const unsigned char *, const R *, R *,      \
                                                cudaStream_t);                                                \
   template cudaError_t launch_floor_fix<R>(long long, const R *, long long, const void *, double, R *,     \

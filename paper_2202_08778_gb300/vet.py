@@ -30,7 +30,14 @@ EXPORTS = (
     "vet_set_timing", "vet_last_timing", "vet_launches_per_closure", "vet_last_error", "vet_closure_noalloc",
     "vet_set_tuning", "vet_get_tuning", "vet_autotune", "vet_batch_create", "vet_batch_destroy", "vet_batch_context",
     "vet_batch_closure", "vet_batch_sync", "vet_batch_autotune", "vet_batch_last_error",
+    "vet_model_create", "vet_model_destroy", "vet_model_num_params", "vet_model_set_params", "vet_model_get_params",
+    "vet_model_get_grads", "vet_model_features", "vet_model_forward", "vet_model_backward", "vet_model_step",
+    "vet_closure_learned", "vet_model_last_timing", "vet_model_last_indicator", "vet_model_last_error",
 )
+
+#: functions whose return value is not a vet_status
+_NOT_STATUS = ("vet_num_directions", "vet_last_error", "vet_launches_per_closure", "vet_batch_context",
+               "vet_batch_last_error", "vet_model_num_params", "vet_model_last_error")
 
 
 class VetError(RuntimeError):
@@ -70,6 +77,7 @@ def load(build_if_missing: bool = True):
             raise RuntimeError(f"libvet is not built ({path} missing); run paper_2202_08778_gb300.build.build()")
         lib = ctypes.CDLL(path)
         vp, i = ctypes.c_void_p, ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
         lib.vet_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Grid), ctypes.POINTER(_Config)]
         lib.vet_destroy.argtypes = [vp]
         lib.vet_num_directions.argtypes = [vp]
@@ -88,7 +96,6 @@ def load(build_if_missing: bool = True):
         lib.vet_launches_per_closure.argtypes = [vp]
         lib.vet_launches_per_closure.restype = i
         lib.vet_closure_noalloc.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Config), vp, vp, vp, vp, vp, vp]
-        ip = ctypes.POINTER(ctypes.c_int)
         lib.vet_set_tuning.argtypes = [vp, i, i]
         lib.vet_get_tuning.argtypes = [vp, ip, ip]
         lib.vet_autotune.argtypes = [vp, vp, vp, vp, ip, ip, vp]
@@ -103,9 +110,24 @@ def load(build_if_missing: bool = True):
         lib.vet_batch_last_error.restype = ctypes.c_char_p
         lib.vet_last_error.argtypes = [vp]
         lib.vet_last_error.restype = ctypes.c_char_p
+        lib.vet_model_create.argtypes = [ctypes.POINTER(vp), i, i]
+        lib.vet_model_destroy.argtypes = [vp]
+        lib.vet_model_num_params.argtypes = [vp]
+        lib.vet_model_num_params.restype = ctypes.c_longlong
+        for name in ("vet_model_set_params", "vet_model_get_params", "vet_model_get_grads"):
+            getattr(lib, name).argtypes = [vp, vp]
+        lib.vet_model_features.argtypes = [vp, ctypes.POINTER(_Grid), i, vp, vp, vp, vp, vp]
+        lib.vet_model_forward.argtypes = [vp, vp, vp]
+        lib.vet_model_backward.argtypes = [vp, vp, vp, ctypes.c_float, vp, vp]
+        f = ctypes.c_float
+        lib.vet_model_step.argtypes = [vp, f, f, f, f, f, vp]
+        lib.vet_closure_learned.argtypes = [vp, vp, vp, vp, vp, vp, f, vp, vp, ip, vp]
+        lib.vet_model_last_timing.argtypes = [vp, ctypes.POINTER(f)]
+        lib.vet_model_last_indicator.argtypes = [vp, vp, vp]
+        lib.vet_model_last_error.argtypes = [vp]
+        lib.vet_model_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("vet_num_directions", "vet_last_error", "vet_launches_per_closure", "vet_batch_context",
-                            "vet_batch_last_error"):
+            if name not in _NOT_STATUS:
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -120,7 +142,8 @@ def _ptr(a, dtype, n, name):
     except ImportError:  # pragma: no cover
         torch = None
     if torch is not None and isinstance(a, torch.Tensor):
-        want = torch.float32 if dtype == np.float32 else torch.float64
+        want = {np.float32: torch.float32, np.float64: torch.float64, np.uint8: torch.uint8,
+                np.int32: torch.int32}[dtype]
         if a.dtype != want:
             raise TypeError(f"{name}: expected {want}, got {a.dtype}")
         if not a.is_contiguous():
@@ -163,6 +186,8 @@ class Context:
         self.ncell = int(nz) * int(ny) * int(nx)
         self.precision = precision
         self.dtype = np.float64 if precision == VET_FP64 else np.float32
+        self.block = int(block)
+        self.h = float(h)
         g = _Grid(int(nx), int(ny), int(nz), int(block), float(h))
         q = (ctypes.c_double * 4)(*[float(v) for v in rot_q])
         cfg = _Config(int(nside), q, int(precision), int(device), int(spin_limit))
@@ -278,10 +303,11 @@ def closure_noalloc(shape, block: int, h: float, nside: int, kappa, S, Ib, f_out
 class _Member(Context):
     """A grid of a Batch: a view of a context the batch owns."""
 
-    def __init__(self, lib, handle, shape):
+    def __init__(self, lib, handle, shape, block):
         self._lib = lib
         self._h = ctypes.c_void_p(handle)
         self.shape = tuple(int(v) for v in shape)
+        self.block = int(block)
         self.ncell = int(np.prod(self.shape))
         self.precision = VET_FP32
         self.dtype = np.float32
@@ -311,7 +337,8 @@ class Batch:
             raise VetError(st, self._lib.vet_last_error(None).decode())
         self._h = h_
         self.n = n
-        self.members = [_Member(self._lib, self._lib.vet_batch_context(self._h, i), problems[i][0]) for i in range(n)]
+        self.members = [_Member(self._lib, self._lib.vet_batch_context(self._h, i), problems[i][0], problems[i][1])
+                        for i in range(n)]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -356,3 +383,132 @@ class Batch:
 
     def sync(self):
         self._check(self._lib.vet_batch_sync(self._h))
+
+
+#: (input, output) channels of the four convolutions for `channels` hidden channels
+def layer_shapes(channels: int = 32):
+    return [(6, channels), (channels, channels), (channels, channels), (channels, 7)]
+
+
+class Model:
+    """vet_model: the learned closure's network, its optimiser state and
+    workspace (include/vet.h).  Parameters cross as a list of (W, b) with
+    W[27][C_out][C_in] and b[C_out] per layer."""
+
+    def __init__(self, channels: int = 32, device: int = 0):
+        self._lib = load()
+        h_ = ctypes.c_void_p()
+        st = self._lib.vet_model_create(ctypes.byref(h_), int(channels), int(device))
+        if st != VET_OK:
+            raise VetError(st, self._lib.vet_model_last_error(None).decode())
+        self._h = h_
+        self.channels = int(channels)
+        self.shapes = layer_shapes(self.channels)
+        self.num_params = int(self._lib.vet_model_num_params(self._h))
+        self.nvol = 0
+        self.ncell = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.vet_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != VET_OK:
+            raise VetError(st, self._lib.vet_model_last_error(self._h).decode())
+
+    def _flat(self, params):
+        parts = []
+        for (W, b), (ci, co) in zip(params, self.shapes):
+            W = np.asarray(W, dtype=np.float32)
+            b = np.asarray(b, dtype=np.float32)
+            if W.shape != (27, co, ci) or b.shape != (co,):
+                raise ValueError(f"layer shapes: expected W {(27, co, ci)}, b {(co,)}; got {W.shape}, {b.shape}")
+            parts += [W.ravel(), b.ravel()]
+        flat = np.ascontiguousarray(np.concatenate(parts))
+        assert flat.size == self.num_params
+        return flat
+
+    def _unflat(self, flat):
+        out, k = [], 0
+        for ci, co in self.shapes:
+            W = flat[k:k + 27 * co * ci].reshape(27, co, ci)
+            k += 27 * co * ci
+            b = flat[k:k + co]
+            k += co
+            out.append((W.copy(), b.copy()))
+        return out
+
+    def set_params(self, params):
+        flat = self._flat(params)
+        self._check(self._lib.vet_model_set_params(self._h, flat.ctypes.data))
+
+    def params(self):
+        flat = np.zeros(self.num_params, dtype=np.float32)
+        self._check(self._lib.vet_model_get_params(self._h, flat.ctypes.data))
+        return self._unflat(flat)
+
+    def grads(self):
+        flat = np.zeros(self.num_params, dtype=np.float32)
+        self._check(self._lib.vet_model_get_grads(self._h, flat.ctypes.data))
+        return self._unflat(flat)
+
+    def features(self, shape, block: int, h: float, kappa, S, E, nvol: int = 1, feat_out=None, stream=None):
+        """Features of nvol stacked volumes of `shape` (device tensors)."""
+        nz, ny, nx = (int(v) for v in shape)
+        n = nvol * nz * ny * nx
+        g = _Grid(nx, ny, nz, int(block), float(h))
+        self._check(self._lib.vet_model_features(
+            self._h, ctypes.byref(g), int(nvol), _ptr(kappa, np.float32, n, "kappa"), _ptr(S, np.float32, n, "S"),
+            _ptr(E, np.float32, n, "E"), _ptr(feat_out, np.float32, 6 * n, "feat_out"), _stream(stream)))
+        self.nvol, self.ncell = int(nvol), n
+        return feat_out
+
+    def forward(self, o_out=None, stream=None):
+        self._check(self._lib.vet_model_forward(self._h, _ptr(o_out, np.float32, 7 * self.ncell, "o_out"),
+                                                _stream(stream)))
+        return o_out
+
+    def backward(self, f_ref, mask=None, lam: float = 0.01, loss_out=None, stream=None):
+        n = self.ncell
+        self._check(self._lib.vet_model_backward(self._h, _ptr(f_ref, np.float32, 6 * n, "f_ref"),
+                                                 _ptr(mask, np.uint8, n, "mask"), float(lam),
+                                                 _ptr(loss_out, np.float64, 1, "loss_out"), _stream(stream)))
+        return loss_out
+
+    def step(self, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+             weight_decay: float = 1e-4, stream=None):
+        self._check(self._lib.vet_model_step(self._h, float(lr), float(beta1), float(beta2), float(eps),
+                                             float(weight_decay), _stream(stream)))
+
+    def closure(self, ctx: Context, kappa, S, E, f_out, Ib=None, threshold: float = 1e-2, block_flags=None,
+                stream=None) -> int:
+        """vet_closure_learned on ctx's grid; returns the number of blocks
+        recomputed by the exact closure."""
+        nc = ctx.ncell
+        nfb = ctypes.c_int(0)
+        nblk = nc // (ctx.block ** 3)
+        st = self._lib.vet_closure_learned(
+            ctx._h, self._h, _ptr(kappa, np.float32, nc, "kappa"), _ptr(S, np.float32, nc, "S"),
+            _ptr(E, np.float32, nc, "E"), _ptr(Ib, np.float32, 6 * ctx.N, "Ib"), float(threshold),
+            _ptr(f_out, np.float32, 6 * nc, "f_out"), _ptr(block_flags, np.int32, nblk, "block_flags"),
+            ctypes.byref(nfb), _stream(stream))
+        self._check(st)
+        return nfb.value
+
+    def last_timing(self):
+        """(network, fallback, whole call) in ms of the last learned closure."""
+        ms = (ctypes.c_float * 3)()
+        self._check(self._lib.vet_model_last_timing(self._h, ms))
+        return tuple(float(v) for v in ms)
+
+    def last_indicator(self, r_out, ncell: int, stream=None):
+        self._check(self._lib.vet_model_last_indicator(self._h, _ptr(r_out, np.float32, ncell, "r_out"),
+                                                       _stream(stream)))
+        return r_out

@@ -14,7 +14,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(vet_\w+)\s*\(", src, flags=re.M))
+        names |= set(re.findall(r"^\s*(?:const\s+)?(?:\w+\s+)*?\w+\s*\**\s*(vet_\w+)\s*\(", src, flags=re.M))
     return names
 
 
