@@ -10,6 +10,10 @@ against the FP64 oracle).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
+The line also carries, at N = 1, a "learned" object: the learned closure
+(network + indicator + exact fallback on flagged blocks) at 256^3 against the
+plain closure on the same GPU, with the network trained in the same run.
+
 Prints one JSON line on rank 0.  With --gpus N > 1 (under torchrun) every
 rank runs an independent replica of the workload on its own GPU (the method
 has no data exchange between replicas); the value is the total over ranks
@@ -58,6 +62,25 @@ def measured_traffic():
     if hashlib.sha256(src).hexdigest() != rec.get("kernel_source_sha256"):
         return None
     return rec.get("bytes_per_launch")
+
+
+def slowest_rank_ms(total_ms: float, world: int, device=None) -> float:
+    """The timed region's length over all ranks: the maximum of every rank's
+    own total (one all-reduce; a barrier after it)."""
+    if world <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, total_ms: float) -> float:
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * world / (total_ms * 1e-3)
 
 
 def measured_peaks():
@@ -149,6 +172,100 @@ def oracle_sample(p, dirs, ndir_sample: int):
         f"trace+moments+closure in FP64")
 
 
+def conv_flops_per_cell():
+    """Multiply-adds x 2 of the four convolutions as stored (padded channels:
+    16 -> 32 -> 32 -> 32 -> 16)."""
+    return 2 * 27 * (16 * 32 + 32 * 32 + 32 * 32 + 32 * 16)
+
+
+def learned_measurement(local_rank):
+    """The learned closure at 256^3 in 16^3 blocks with 192 directions (the
+    lognormal generator, seed 3) against the plain closure on the same GPU.
+    The network is trained here, on 64^3 snapshots of the same generator
+    labelled by the exact closure (a bounded sample of the specified 2000)."""
+    import numpy as np
+    import torch
+
+    from paper_2202_08778_gb300 import learned, synth, vet
+
+    dev = torch.device("cuda", local_rank)
+    nt, B, ns = 64, 16, 4
+    ntrain, steps, batch = 64, 1500, 4
+    t0 = time.perf_counter()
+    ctx_t = vet.Context((nt,) * 3, B, 1.0 / nt, ns, synth.rotation_quaternion(10000), device=local_rank)
+    data = learned.snapshots(ctx_t, range(10000, 10000 + ntrain), nt, B, ns)
+    t_data = time.perf_counter() - t0
+    model = vet.Model(device=local_rank)
+    model.set_params(learned.init_params(32, seed=0))
+    t0 = time.perf_counter()
+    losses = learned.train(model, data, (nt,) * 3, B, 1.0 / nt, steps, batch=batch)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    del data, ctx_t
+
+    n = 256
+    p = synth.lognormal_problem(n=n, B=B, nside=ns, seed=3)
+    ctx = vet.Context(p["kappa"].shape, B, p["h"], ns, p["q"], device=local_rank)
+    kappa = torch.from_numpy(np.ascontiguousarray(p["kappa"].astype(np.float32))).to(dev)
+    S = torch.from_numpy(np.ascontiguousarray(p["S"].astype(np.float32))).to(dev)
+    N = n ** 3
+    nblk = N // B ** 3
+    f_plain = torch.empty(6 * N, device=dev)
+    M = torch.empty(10 * N, device=dev)
+    ctx.autotune(kappa, S)
+    ctx.closure(kappa, S, None, f_plain, M)
+    E = M[:N].clone()
+    del M
+    ctx.set_timing(True)
+    plain = []
+    for _ in range(5):  # the working set (3 GB of faces) is far larger than L2
+        ctx.closure(kappa, S, None, f_plain)
+        plain.append(ctx.last_timing()[3])
+    ctx.set_timing(False)
+    plain_ms = statistics.median(plain)
+
+    f = torch.empty(6 * N, device=dev)
+
+    def run(thr):
+        model.closure(ctx, kappa, S, E, f, threshold=thr)
+        ts = []
+        nfb = 0
+        for _ in range(3):
+            nfb = model.closure(ctx, kappa, S, E, f, threshold=thr)
+            ts.append(model.last_timing())
+        ctx.sync()
+        return nfb, [statistics.median(t[i] for t in ts) for i in range(4)]
+
+    def err_stats(fg):
+        e = (fg - f_plain).abs().view(6, -1).amax(0)
+        q = torch.quantile(e[::97].double(), torch.tensor([0.5, 0.99], dtype=torch.float64, device=dev))
+        return {"mean": float(e.double().mean()), "p50": float(q[0]), "p99": float(q[1]), "max": float(e.max())}
+
+    nfb_inf, t_inf = run(float("inf"))
+    net_err = err_stats(f)
+    thr = 1e-2
+    nfb, t_thr = run(thr)
+    fb_err = float((f - f_plain).abs().max())
+    iso = torch.zeros_like(f).view(6, -1)
+    iso[:3] = 1.0 / 3.0
+    edd = (iso - f_plain.view(6, -1)).abs().amax(0)
+    tflops = conv_flops_per_cell() * N / (t_inf[3] * 1e-3) / 1e12
+    peak = float(measured_peaks().get("bf16_tflops", 1900.0))
+    return {
+        "workload": "lognormal256_B16_nside4 (seed 3)", "plain_closure_ms": plain_ms,
+        "threshold": thr, "fallback_blocks": nfb, "blocks": nblk, "ms": t_thr[2],
+        "ms_network": t_thr[0], "ms_fallback": t_thr[1], "speedup_vs_plain": plain_ms / t_thr[2],
+        "max_abs_df_vs_plain": fb_err,
+        "network_only": {"ms": t_inf[2], "speedup_vs_plain": plain_ms / t_inf[2], "abs_df_vs_plain": net_err},
+        "eddington_I_over_3": {"mean": float(edd.double().mean()), "max": float(edd.max())},
+        "conv_roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                          "frac": tflops / peak, "kernel": "conv3d_kernel (4 layers, mma.sync BF16)",
+                          "algorithmic": f"{conv_flops_per_cell()} FLOP per cell (padded channels) x {N} cells"},
+        "train": {"snapshots": ntrain, "shape": [nt] * 3, "steps": steps, "batch": batch,
+                  "seconds": t_train, "data_seconds": t_data, "final_loss": losses[-1]},
+    }
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm (host cores, rank 0 only)."""
     if rank != 0:
@@ -220,16 +337,10 @@ def run_ours(args, rank, world, local_rank):
             phase.append(ctx.last_timing())
         torch.cuda.synchronize(dev)
     ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
+    total_ms = slowest_rank_ms(sum(ms), world, dev)
     ctx.set_timing(False)
     ms_step = total_ms / args.steps
-    updates = float(n) * N * args.steps * world
-    value = updates / (total_ms * 1e-3) / 1e9
+    value = whole_job_rate(float(n) * N * args.steps, world, total_ms) / 1e9
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     kp = torch.from_numpy(k_h).pin_memory()
@@ -271,6 +382,9 @@ def run_ours(args, rank, world, local_rank):
     if clocks is not None:
         line["clocks"] = clocks
 
+    if rank == 0 and world == 1 and not args.no_learned:
+        line["learned"] = learned_measurement(local_rank)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0))
         nsub = min(N, 2 * cores)
@@ -288,6 +402,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

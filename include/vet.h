@@ -289,8 +289,9 @@ vet_status vet_closure_learned(vet_ctx *ctx, vet_model *model, const float *kapp
 
 /* Device time of the last vet_closure_learned, in milliseconds: ms[0] the
  * network (features, convolutions, indicator and block list), ms[1] the
- * fallback (exact closure on the flagged blocks), ms[2] the whole call. */
-vet_status vet_model_last_timing(vet_model *model, float ms[3]);
+ * fallback (exact closure on the flagged blocks), ms[2] the whole call,
+ * ms[3] the four convolutions alone (part of ms[0]). */
+vet_status vet_model_last_timing(vet_model *model, float ms[4]);
 
 /* Individual indicator values of the last vet_closure_learned call's grid:
  * r_out [cells] FP32, device.  For inspection. */

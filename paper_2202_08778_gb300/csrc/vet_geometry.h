@@ -111,10 +111,12 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   merge_events(ev, n);
   for (int i = 0; i < 3 * B; ++i) cpos[i] = kNever;
   double prev = 0.0;
+  int off = 0;
   for (int e = 0; e < n; ++e) {
     cpos[ev[e].axis * B + ev[e].m] = (int16_t)e;
     cev[e].len = R((ev[e].t - prev) * scale);
-    cev[e].delta = -sgn[ev[e].axis] * cstride[ev[e].axis];
+    cev[e].off = off;
+    off -= sgn[ev[e].axis] * cstride[ev[e].axis];  // crossing the plane moves one cell upwind
     prev = ev[e].t;
   }
   // node rays: planes at t = m/|n_a|, m = 1..B
@@ -128,10 +130,12 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
     for (int m = 1; m <= B; ++m) npos[a * (B + 1) + m] = kNever;
   }
   prev = 0.0;
+  off = 0;
   for (int e = 0; e < n; ++e) {
     npos[ev[e].axis * (B + 1) + ev[e].m] = (int16_t)e;
     nev[e].len = R((ev[e].t - prev) * scale);
-    nev[e].delta = -sgn[ev[e].axis] * nstride[ev[e].axis];
+    nev[e].off = off;
+    off -= sgn[ev[e].axis] * nstride[ev[e].axis];
     prev = ev[e].t;
   }
   // exit tables: leaving through axis a at depth D, the in-plane upwind-frame

@@ -43,11 +43,13 @@ struct TplHead {
 };
 
 // One event of a ray template: the length of the segment that ends at it,
-// scaled by -h log2(e), and the tile-index step taken there.
+// scaled by -h log2(e), and the tile-index offset, from the ray's start cell,
+// of the cell that segment crosses (0 for the first segment).  Rays are
+// marched downwind, from their last event back to the start.
 template <typename R>
 struct alignas(2 * sizeof(R)) TplEvent {
   R len;
-  int delta;
+  int off;
 };
 
 struct TplLayout {

@@ -29,16 +29,22 @@ template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<double> { using T = double2; };
 template <typename R> using vec2_t = typename Vec2<R>::T;
 
-// exp(-x) and 1 - exp(-x) for the optical depth x >= 0 of one segment, given
-// y = -x log2(e) (segment lengths are stored pre-scaled by -h log2(e)).
-//   FP32: for x < 1/2 both come from a polynomial, 1 - 2^y = y q(y) with q of
-//   degree 5 fitted by weighted least squares (relative error 1.4e-9 in exact
-//   arithmetic, i.e. FP32 rounding dominates): 1 - e would cancel there, and
-//   the MUFU's 1.5e-7 error on e compounds along long thin paths (1.1e-5 on I
-//   after ~300 thin segments of the shadow workload, measured); for x >= 1/2,
-//   e comes from the MUFU (ex2.approx) and 1 - e is well conditioned.
-//   FP64: the CUDA math library's exp2 and expm1.
-__device__ __forceinline__ void attenuation(float y, float &e, float &om) {
+// One segment of optical depth x >= 0, given y = -x log2(e) (segment lengths
+// are stored pre-scaled by -h log2(e)), updates I exactly over a cell of
+// source S: I <- I + (S - I)(1 - e^-x) = S + (I - S) e^-x.  Each form is
+// evaluated where it cannot cancel:
+//   thin (x < 1/2): I + (S - I) om with om = 1 - e^-x from a polynomial,
+//     om = y q(y), q of degree 5 fitted by weighted least squares (relative
+//     error 1.4e-9 in exact arithmetic): the other form would round S to its
+//     ulp before subtracting almost all of it when S >> I, and 1 - e would
+//     cancel;
+//   thick (x >= 1/2): S + (I - S) e with e from the MUFU (ex2.approx); here
+//     the first form would cancel when I >> S.
+// Thin segments never use the MUFU, whose 1.5e-7 error is not zero-mean and
+// would compound along long thin paths.  FP64: exp2 and expm1 of the CUDA
+// math library in the same two forms.
+__device__ __forceinline__ float seg_weight(float y, bool &thin) {
+  float e;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
   float q = -1.243609540706334e-04f;
   q = fmaf(q, y, -1.3099410122314181e-03f);
@@ -46,42 +52,38 @@ __device__ __forceinline__ void attenuation(float y, float &e, float &om) {
   q = fmaf(q, y, -5.550262416593144e-02f);
   q = fmaf(q, y, -2.4022641347108148e-01f);
   q = fmaf(q, y, -6.931471795930371e-01f);
-  const float p = q * y;
-  const bool thin = y > -0.7213475204444817f;  // x < 1/2
-  om = thin ? p : 1.0f - e;
-  e = thin ? 1.0f - p : e;
+  thin = y > -0.7213475204444817f;  // x < 1/2
+  return thin ? q * y : e;
 }
 
-__device__ __forceinline__ void attenuation(double y, double &e, double &om) {
-  e = exp2(y);
-  om = -expm1(y * 0.6931471805599453094);
-}
-
-// Exact update over piecewise-constant cells, marching backward from the
-// ray's start: after the loop, I(start) = acc + T * I(entry point).
-template <typename R>
-__device__ __forceinline__ void segment(const vec2_t<R> *__restrict__ tile, int &idx, const TplEvent<R> &ev, R &acc,
-                                        R &T) {
-  const vec2_t<R> ks = tile[idx];
-  idx += ev.delta;
-  R ex, om;
-  attenuation(ks.x * ev.len, ex, om);
-  acc = fma(ks.y * om, T, acc);
-  T *= ex;
+__device__ __forceinline__ double seg_weight(double y, bool &thin) {
+  thin = y > -0.7213475204444817;
+  return thin ? -expm1(y * 0.6931471805599453094) : exp2(y);
 }
 
 template <typename R>
-__device__ __forceinline__ void march(const vec2_t<R> *__restrict__ tile, int idx, int last,
-                                      const TplEvent<R> *__restrict__ ev, R &acc, R &T) {
-  acc = R(0);
-  T = R(1);
-  int e = 0;
-  for (; e < last; e += 2) {  // two segments per trip
-    const TplEvent<R> e0 = ev[e], e1 = ev[e + 1];
-    segment<R>(tile, idx, e0, acc, T);
-    segment<R>(tile, idx, e1, acc, T);
+__device__ __forceinline__ void segment(const vec2_t<R> *__restrict__ tile, int idx0, const TplEvent<R> &ev, R &I) {
+  const vec2_t<R> ks = tile[idx0 + ev.off];
+  bool thin;
+  const R w = seg_weight(ks.x * ev.len, thin);
+  const R base = thin ? I : ks.y, other = thin ? ks.y : I;
+  I = fma(other - base, w, base);
+}
+
+// Intensity at a ray's start point: entering with I at the upwind end of
+// segment `last`, the segments last, last-1, ..., 0 are crossed downwind.
+// last = -1 (a start point on the upwind face) returns I unchanged.
+template <typename R>
+__device__ __forceinline__ R march(const vec2_t<R> *__restrict__ tile, int idx0, int last,
+                                   const TplEvent<R> *__restrict__ ev, R I) {
+  int e = last;
+  for (; e > 0; e -= 2) {  // two segments per trip
+    const TplEvent<R> e0 = ev[e], e1 = ev[e - 1];
+    segment<R>(tile, idx0, e0, I);
+    segment<R>(tile, idx0, e1, I);
   }
-  if (e == last) segment<R>(tile, idx, ev[e], acc, T);
+  if (e == 0) segment<R>(tile, idx0, ev[0], I);
+  return I;
 }
 
 // Typed view of one direction's template blob.
@@ -312,26 +314,23 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     const R *fin = reinterpret_cast<const R *>(slots + sb * j + TL.bytes);
     const int a = n / NN, r = n - a * NN;
     const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
-    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-    int L[3];
-    L[a] = B;
-    L[b] = ub;
-    L[c] = uc;
-    int last = T.npos[L[0]], ae = 0;
-    if (T.npos[N1 + L[1]] < last) { last = T.npos[N1 + L[1]]; ae = 1; }
-    if (T.npos[2 * N1 + L[2]] < last) { last = T.npos[2 * N1 + L[2]]; ae = 2; }
-    R acc = R(0), Tr = R(1);
+    // upwind-frame node coordinates (L0, L1, L2): B along the face's axis
+    const int L0 = a == 0 ? B : ub;
+    const int L1 = a == 1 ? B : (a == 0 ? ub : uc);
+    const int L2 = a == 2 ? B : uc;
+    const int p0 = T.npos[L0], p1 = T.npos[N1 + L1], p2 = T.npos[2 * N1 + L2];
+    int last = p0, ae = 0, la = L0, lb = L1, lc = L2;
+    if (p1 < last) { last = p1; ae = 1; la = L1; lb = L0; }
+    if (p2 < last) { last = p2; ae = 2; la = L2; lb = L0; lc = L1; }
+    const int row = (ae * 2) * N1 + la;
+    R I = face_value<R>(fin, g.fstride, B, ae, lb, lc, T.nk[row], T.nk[row + N1], T.nw[row], T.nw[row + N1]);
     if (last >= 0) {  // then every L >= 1 and the start cell is inside the block
-      int cell[3];
-      for (int q = 0; q < 3; ++q) cell[q] = T.h->sgn[q] > 0 ? L[q] - 1 : B - L[q];
-      march<R>(tile, cell[0] + ts.sy * cell[1] + ts.sz * cell[2], last, T.nev, acc, Tr);
+      const int c0 = T.h->sgn[0] > 0 ? L0 - 1 : B - L0;
+      const int c1 = T.h->sgn[1] > 0 ? L1 - 1 : B - L1;
+      const int c2 = T.h->sgn[2] > 0 ? L2 - 1 : B - L2;
+      I = march<R>(tile, c0 + ts.sy * c1 + ts.sz * c2, last, T.nev, I);
     }
-    const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
-    const int row = (ae * 2) * N1 + L[ae];
-    const R Iin = face_value<R>(fin, g.fstride, B, ae, L[eb], L[ec], T.nk[row], T.nk[row + N1], T.nw[row],
-                                T.nw[row + N1]);
-    faces[(((long long)(it.dir_begin + j) * nblk + it.block) * 3 + a) * g.fstride + ub * W + uc] =
-        fma(Tr, Iin, acc);
+    faces[(((long long)(it.dir_begin + j) * nblk + it.block) * 3 + a) * g.fstride + ub * W + uc] = I;
   }
 }
 
@@ -437,20 +436,18 @@ __global__ void __launch_bounds__(kCellThreads, 2)
       for (int j = 0; j < nd; ++j) {
         const Tpl<R> T(buf + sb * j, TL);
         const R *fin = reinterpret_cast<const R *>(buf + sb * j + TL.bytes);
-        int l[3];
-        l[0] = T.h->sgn[0] > 0 ? cx : B - 1 - cx;
-        l[1] = T.h->sgn[1] > 0 ? cy : B - 1 - cy;
-        l[2] = T.h->sgn[2] > 0 ? cz : B - 1 - cz;
-        int last = T.cpos[l[0]], ae = 0;
-        if (T.cpos[B + l[1]] < last) { last = T.cpos[B + l[1]]; ae = 1; }
-        if (T.cpos[2 * B + l[2]] < last) { last = T.cpos[2 * B + l[2]]; ae = 2; }
-        R acc, Tr;
-        march<R>(tile, tc, last, T.cev, acc, Tr);
-        const int eb = ae == 0 ? 1 : 0, ec = ae == 2 ? 1 : 2;
-        const int row = (ae * 2) * B + l[ae];
-        const R Iin = face_value<R>(fin, fstride, B, ae, l[eb], l[ec], T.ck[row], T.ck[row + B], T.cw[row],
-                                    T.cw[row + B]);
-        const R I = fma(Tr, Iin, acc);
+        // upwind-frame coordinates; the exit axis ae is the one whose plane
+        // event comes first, (lb, lc) the other two in increasing axis order
+        const int l0 = T.h->sgn[0] > 0 ? cx : B - 1 - cx;
+        const int l1 = T.h->sgn[1] > 0 ? cy : B - 1 - cy;
+        const int l2 = T.h->sgn[2] > 0 ? cz : B - 1 - cz;
+        const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
+        int last = p0, ae = 0, la = l0, lb = l1, lc = l2;
+        if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; }
+        if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; }
+        const int row = (ae * 2) * B + la;
+        const R Iin = face_value<R>(fin, fstride, B, ae, lb, lc, T.ck[row], T.ck[row + B], T.cw[row], T.cw[row + B]);
+        const R I = march<R>(tile, tc, last, T.cev, Iin);
         if (MODE == 1) {
           I_out[(long long)T.h->ext * g.ncell + gc] = I;
         } else {

@@ -46,7 +46,7 @@ struct vet_model {
   cnn::Vol V{0, 0, 0, 0};
   bool have_features = false, have_forward = false, have_backward = false;
   long long last_r_cells = 0;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool timed = false;
   std::string err;
 };
@@ -281,7 +281,7 @@ VET_API vet_status vet_model_create(vet_model **out, int channels, int device) {
   if (!e) e = cudaMalloc((void **)&m->loss, sizeof(double));
   if (!e) e = cudaMalloc((void **)&m->nlist, sizeof(int));
   if (!e) e = cudaMallocHost((void **)&m->h_nlist, sizeof(int));
-  for (int i = 0; i < 4 && !e; ++i) e = cudaEventCreate(&m->ev[i]);
+  for (int i = 0; i < 5 && !e; ++i) e = cudaEventCreate(&m->ev[i]);
   for (float *ptr : {m->p, m->g, m->m, m->v})
     if (!e) e = cudaMemset(ptr, 0, sizeof(float) * off);
   if (!e) e = cudaMemset(m->wb, 0, sizeof(bf16) * woff);
@@ -452,7 +452,9 @@ VET_API vet_status vet_closure_learned(vet_ctx *ctx, vet_model *m, const float *
   m->timed = false;
   cudaError_t e = cudaEventRecord(m->ev[0], st);
   if (!e) e = cnn::features(kappa, S, E, V, g.block, g.h, m->sums, m->bstat, m->x0, nullptr, st);
+  if (!e) e = cudaEventRecord(m->ev[3], st);
   if (!e) e = run_forward(m, V, false, st);
+  if (!e) e = cudaEventRecord(m->ev[4], st);
   if (!e) e = cnn::indicator(m->o, V, g.block, threshold, f_out, m->r, m->flags, st);
   if (!e) e = cnn::compact_flags(m->flags, ci.nblk, m->list, m->nlist, st);
   if (!e && block_flags_out)
@@ -476,7 +478,7 @@ VET_API vet_status vet_closure_learned(vet_ctx *ctx, vet_model *m, const float *
   return VET_OK;
 }
 
-VET_API vet_status vet_model_last_timing(vet_model *m, float ms[3]) {
+VET_API vet_status vet_model_last_timing(vet_model *m, float ms[4]) {
   if (!m || !ms) return VET_EINVAL;
   if (!m->timed) return fail(m, VET_EINVAL, "no timed learned closure");
   DevGuard dg(m->device);
@@ -484,6 +486,7 @@ VET_API vet_status vet_model_last_timing(vet_model *m, float ms[3]) {
   if (!e) e = cudaEventElapsedTime(&ms[0], m->ev[0], m->ev[1]);
   if (!e) e = cudaEventElapsedTime(&ms[1], m->ev[1], m->ev[2]);
   if (!e) e = cudaEventElapsedTime(&ms[2], m->ev[0], m->ev[2]);
+  if (!e) e = cudaEventElapsedTime(&ms[3], m->ev[3], m->ev[4]);
   if (e) return cuda_fail(m, e, "event timing");
   return VET_OK;
 }

@@ -1,0 +1,82 @@
+"""Training and evaluation helpers of the learned closure (the network and
+its kernels are in libvet; see include/vet.h).
+
+The training data are the method's own output: seeded lognormal snapshots
+(synth.lognormal_problem) whose f and E come from the exact GPU closure.
+Every step runs in libvet's kernels; this module only sequences the calls.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import synth, vet
+
+
+def init_params(channels: int = 32, seed: int = 0):
+    """He-uniform weights (bound sqrt(6 / fan_in), fan_in = 27 C_in); the
+    last layer starts at zero with the error output's bias at log(1e-2), so
+    the untrained network is the isotropic closure I/3."""
+    rng = np.random.default_rng(seed)
+    out = []
+    shapes = vet.layer_shapes(channels)
+    for li, (ci, co) in enumerate(shapes):
+        if li < len(shapes) - 1:
+            bound = math.sqrt(6.0 / (27 * ci))
+            W = rng.uniform(-bound, bound, (27, co, ci))
+        else:
+            W = np.zeros((27, co, ci))
+        b = np.zeros(co)
+        if li == len(shapes) - 1:
+            b[6] = math.log(1e-2)
+        out.append((W, b))
+    return out
+
+
+def snapshots(ctx, seeds, n: int, B: int, nside: int):
+    """Device tensors (kappa, S, E, f) [len(seeds)][...] of lognormal n^3
+    snapshots, labelled by the exact closure of ctx (same grid and
+    directions)."""
+    import torch
+
+    N = n ** 3
+    ks, ss, es, fs = [], [], [], []
+    for s in seeds:
+        p = synth.lognormal_problem(n=n, B=B, nside=nside, seed=int(s))
+        k = torch.from_numpy(np.ascontiguousarray(p["kappa"].astype(np.float32))).cuda()
+        S = torch.from_numpy(np.ascontiguousarray(p["S"].astype(np.float32))).cuda()
+        f = torch.empty(6 * N, device="cuda")
+        M = torch.empty(10 * N, device="cuda")
+        ctx.closure(k, S, None, f, M)
+        ks.append(k)
+        ss.append(S)
+        es.append(M[:N].clone())
+        fs.append(f)
+    ctx.sync()
+    return tuple(torch.stack(x) for x in (ks, ss, es, fs))
+
+
+def train(model, data, shape, B: int, h: float, steps: int, batch: int = 4, lr_max: float = 2e-3,
+          lr_min: float = 1e-4, lam: float = 2e-3, seed: int = 0, log_every: int = 0):
+    """AdamW with a cosine learning-rate schedule over random batches of the
+    snapshots.  Returns the losses sampled every `log_every` steps (and the
+    last one)."""
+    import torch
+
+    k_all, s_all, e_all, f_all = data
+    n = k_all.shape[0]
+    rng = np.random.default_rng(seed)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    losses = []
+    for it in range(steps):
+        idx = torch.from_numpy(rng.choice(n, batch, replace=False)).cuda()
+        k, S, E, f = (x.index_select(0, idx).contiguous() for x in (k_all, s_all, e_all, f_all))
+        model.features(shape, B, h, k, S, E, nvol=batch)
+        model.forward()
+        model.backward(f, lam=lam, loss_out=loss)
+        lr = lr_min + 0.5 * (lr_max - lr_min) * (1.0 + math.cos(math.pi * it / steps))
+        model.step(lr=lr)
+        if (log_every and it % log_every == 0) or it == steps - 1:
+            losses.append(float(loss.item()))
+    return losses

@@ -503,8 +503,9 @@ class Model:
         return nfb.value
 
     def last_timing(self):
-        """(network, fallback, whole call) in ms of the last learned closure."""
-        ms = (ctypes.c_float * 3)()
+        """(network, fallback, whole call, convolutions) in ms of the last
+        learned closure."""
+        ms = (ctypes.c_float * 4)()
         self._check(self._lib.vet_model_last_timing(self._h, ms))
         return tuple(float(v) for v in ms)
 

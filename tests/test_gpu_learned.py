@@ -4,16 +4,17 @@ AdamW's first-step identity, its indicator against closed forms, and the
 trained network plus exact fallback against the ray-traced closure.
 
 Tolerances.  The kernels round features, weights and activations to BF16
-(8 significant bits, relative rounding error <= 2^-9) and accumulate in FP32.
-Weights are rounded to BF16 on the host before both sides see them, so the
-differences left are the BF16 rounding of the 6 input features and of the
-three hidden activations.  Through layers whose gains are O(1) (He
-initialisation) these add up to a few times 2^-9 of the output scale: the
-forward test asks for a maximum error below 2e-2 and an RMS error below
-5e-3 of the RMS output.  Gradients see the same roundings plus the BF16
-rounding of the output gradient and of the back-propagated gradients: each
-layer's weight gradient must agree to 3e-2 in relative Frobenius norm and to
-cosine similarity 0.999.
+(8 significant bits, relative rounding error <= 2^-9 = 2e-3 per value) and
+accumulate in FP32.  Weights are rounded to BF16 on the host before both sides
+see them, so the differences left are the BF16 rounding of the 6 input
+features, of the three hidden activations and (backward) of the propagated
+gradients.  Each output sums 27 x C_in such terms with independent rounding
+errors, so the relative error of a sum is about 2^-9 / sqrt(27 C_in) ~ 1e-4
+per layer, not 2^-9: measured on GB300, the forward pass is within 3.0e-4 of
+the largest output (RMS 1.9e-4 of the RMS output), the loss within 1.1e-5
+relative and every layer's gradient within 1.3e-4 in relative Frobenius norm.
+The bounds below are about 6x those figures: a wrong tap, channel or sign
+moves them by O(1).
 """
 import math
 
@@ -109,8 +110,8 @@ def test_forward_matches_oracle():
     err = np.abs(got - ref)
     rms = math.sqrt((err ** 2).mean()) / math.sqrt((ref ** 2).mean())
     print(f"forward: max |o| {scale:.3f}, max error {err.max() / scale:.2e} of max, rms error {rms:.2e} of rms")
-    assert err.max() < 2e-2 * scale
-    assert rms < 5e-3
+    assert err.max() < 2e-3 * scale
+    assert rms < 1e-3
 
 
 def test_backward_matches_oracle():
@@ -137,14 +138,14 @@ def test_backward_matches_oracle():
         g_ref = gv if g_ref is None else [(a + c, b + d) for (a, b), (c, d) in zip(g_ref, gv)]
     lg = float(loss.item())
     print(f"loss gpu {lg:.6e} oracle {L:.6e}")
-    assert abs(lg - L) < 1e-2 * L
+    assert abs(lg - L) < 1e-4 * L
     for li, ((gw, gb), (rw, rb)) in enumerate(zip(g_gpu, g_ref)):
         a = np.concatenate([gw.ravel(), gb.ravel()]).astype(np.float64)
         r = np.concatenate([rw.ravel(), rb.ravel()])
         rel = np.linalg.norm(a - r) / np.linalg.norm(r)
         cos = a @ r / (np.linalg.norm(a) * np.linalg.norm(r))
         print(f"layer {li}: gradient rel error {rel:.2e}, cosine {cos:.6f}")
-        assert rel < 3e-2 and cos > 0.999
+        assert rel < 1e-3 and cos > 0.99999
 
 
 def test_adamw_first_step_identity():
@@ -306,3 +307,8 @@ def test_learned_closure_with_fallback(trained):
         assert np.array_equal(got[:, cell_flag], ref[:, cell_flag])
         err = np.abs(got - ref).max()
         print(f"held-out {v}: {nfb}/{nblk} blocks recomputed, max |f - f_traced| = {err:.3e}")
+    # without fallback the result is the network's tensor everywhere
+    nfb = m.closure(ctx, held[0][0], held[1][0], held[2][0], f, threshold=float("inf"), block_flags=flags)
+    assert nfb == 0 and int(flags.sum()) == 0
+    f_net = _net_f(m, held[0][0], held[1][0], held[2][0])
+    assert np.abs(f.cpu().numpy().reshape(6, -1) - f_net).max() < 1e-6
