@@ -99,6 +99,11 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   }
   hd->w = R(d[3]);
   hd->ext = ext;
+  {
+    const double w = d[3], x = d[0], y = d[1], z = d[2];
+    const double c[10] = {w, w * x, w * y, w * z, w * x * x, w * y * y, w * z * z, w * x * y, w * x * z, w * y * z};
+    for (int m = 0; m < 10; ++m) hd->c[m] = R(c[m]);
+  }
   const TileShape ct = cell_tile(B), nt = node_tile(B);
   const int cstride[3] = {1, ct.sy, ct.sz};  // cell rays walk the cell-pass tile
   const int nstride[3] = {1, nt.sy, nt.sz};  // node rays walk the face-pass tile
@@ -115,7 +120,7 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   for (int e = 0; e < n; ++e) {
     cpos[ev[e].axis * B + ev[e].m] = (int16_t)e;
     cev[e].len = R((ev[e].t - prev) * scale);
-    cev[e].off = off;
+    cev[e].off = off * (int)(2 * sizeof(R));  // bytes: one (kappa, S) pair per tile cell
     off -= sgn[ev[e].axis] * cstride[ev[e].axis];  // crossing the plane moves one cell upwind
     prev = ev[e].t;
   }
@@ -134,7 +139,7 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   for (int e = 0; e < n; ++e) {
     npos[ev[e].axis * (B + 1) + ev[e].m] = (int16_t)e;
     nev[e].len = R((ev[e].t - prev) * scale);
-    nev[e].off = off;
+    nev[e].off = off * (int)(2 * sizeof(R));
     off -= sgn[ev[e].axis] * nstride[ev[e].axis];
     prev = ev[e].t;
   }

@@ -40,12 +40,17 @@ struct TplHead {
   R w;        // quadrature weight 4 pi / N
   int sgn[3]; // +1 if n_a >= 0 (a zero component counts as positive) else -1
   int ext;    // index of this direction in the documented HEALPix order
+  // quadrature coefficients w (1, nx, ny, nz, nx nx, ny ny, nz nz, nx ny,
+  // nx nz, ny nz) of E, F and P (Eqs. 10-12, c = 1), rounded once from FP64;
+  // two unused entries keep the array a multiple of 16 bytes
+  alignas(16) R c[12];
 };
 
 // One event of a ray template: the length of the segment that ends at it,
-// scaled by -h log2(e), and the tile-index offset, from the ray's start cell,
-// of the cell that segment crosses (0 for the first segment).  Rays are
-// marched downwind, from their last event back to the start.
+// scaled by -h log2(e), and the byte offset in the shared-memory tile, from
+// the ray's start cell, of the cell that segment crosses (0 for the first
+// segment).  Rays are marched downwind, from their last event back to the
+// start.
 template <typename R>
 struct alignas(2 * sizeof(R)) TplEvent {
   R len;

@@ -31,43 +31,43 @@ template <typename R> using vec2_t = typename Vec2<R>::T;
 
 // One segment of optical depth x >= 0, given y = -x log2(e) (segment lengths
 // are stored pre-scaled by -h log2(e)), updates I exactly over a cell of
-// source S: I <- I + (S - I)(1 - e^-x) = S + (I - S) e^-x.  Each form is
-// evaluated where it cannot cancel:
-//   thin (x < 1/2): I + (S - I) om with om = 1 - e^-x from a polynomial,
-//     om = y q(y), q of degree 5 fitted by weighted least squares (relative
-//     error 1.4e-9 in exact arithmetic): the other form would round S to its
-//     ulp before subtracting almost all of it when S >> I, and 1 - e would
-//     cancel;
-//   thick (x >= 1/2): S + (I - S) e with e from the MUFU (ex2.approx); here
+// source S: I <- I - (I - S)(1 - e^-x) = S + (I - S) e^-x.  Each form is
+// evaluated where it cannot cancel, as I' = fma(I - S, w, base):
+//   thin (x < 1/2): base = I, w = -(1 - e^-x) = y q(y) with q of degree 4
+//     fitted for relative error by Lawson's iteratively reweighted least
+//     squares (7.7e-8 in exact arithmetic, the level of FP32 rounding): the
+//     other form would round S to its ulp before subtracting almost all of
+//     it when S >> I, and 1 - e would cancel;
+//   thick (x >= 1/2): base = S, w = e^-x from the MUFU (ex2.approx); here
 //     the first form would cancel when I >> S.
 // Thin segments never use the MUFU, whose 1.5e-7 error is not zero-mean and
-// would compound along long thin paths.  FP64: exp2 and expm1 of the CUDA
+// would compound along long thin paths.  FP64: expm1 and exp2 of the CUDA
 // math library in the same two forms.
 __device__ __forceinline__ float seg_weight(float y, bool &thin) {
   float e;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
-  float q = -1.243609540706334e-04f;
-  q = fmaf(q, y, -1.3099410122314181e-03f);
-  q = fmaf(q, y, -9.60941463103728e-03f);
-  q = fmaf(q, y, -5.550262416593144e-02f);
-  q = fmaf(q, y, -2.4022641347108148e-01f);
-  q = fmaf(q, y, -6.931471795930371e-01f);
+  float q = 1.0833843353054956e-03f;
+  q = fmaf(q, y, 9.4645342235962007e-03f);
+  q = fmaf(q, y, 5.5464640186780434e-02f);
+  q = fmaf(q, y, 2.4022290282685121e-01f);
+  q = fmaf(q, y, 6.9314712699664371e-01f);
   thin = y > -0.7213475204444817f;  // x < 1/2
   return thin ? q * y : e;
 }
 
 __device__ __forceinline__ double seg_weight(double y, bool &thin) {
   thin = y > -0.7213475204444817;
-  return thin ? -expm1(y * 0.6931471805599453094) : exp2(y);
+  return thin ? expm1(y * 0.6931471805599453094) : exp2(y);
 }
 
+// tb: byte address of the ray's start cell in the tile; ev.off is the byte
+// offset of the segment's cell from it.
 template <typename R>
-__device__ __forceinline__ void segment(const vec2_t<R> *__restrict__ tile, int idx0, const TplEvent<R> &ev, R &I) {
-  const vec2_t<R> ks = tile[idx0 + ev.off];
+__device__ __forceinline__ void segment(const unsigned char *__restrict__ tb, const TplEvent<R> &ev, R &I) {
+  const vec2_t<R> ks = *reinterpret_cast<const vec2_t<R> *>(tb + ev.off);
   bool thin;
   const R w = seg_weight(ks.x * ev.len, thin);
-  const R base = thin ? I : ks.y, other = thin ? ks.y : I;
-  I = fma(other - base, w, base);
+  I = fma(I - ks.y, w, thin ? I : ks.y);
 }
 
 // Intensity at a ray's start point: entering with I at the upwind end of
@@ -76,13 +76,14 @@ __device__ __forceinline__ void segment(const vec2_t<R> *__restrict__ tile, int 
 template <typename R>
 __device__ __forceinline__ R march(const vec2_t<R> *__restrict__ tile, int idx0, int last,
                                    const TplEvent<R> *__restrict__ ev, R I) {
+  const unsigned char *tb = reinterpret_cast<const unsigned char *>(tile + idx0);
   int e = last;
   for (; e > 0; e -= 2) {  // two segments per trip
     const TplEvent<R> e0 = ev[e], e1 = ev[e - 1];
-    segment<R>(tile, idx0, e0, I);
-    segment<R>(tile, idx0, e1, I);
+    segment<R>(tb, e0, I);
+    segment<R>(tb, e1, I);
   }
-  if (e == 0) segment<R>(tile, idx0, ev[0], I);
+  if (e == 0) segment<R>(tb, ev[0], I);
   return I;
 }
 
@@ -451,20 +452,10 @@ __global__ void __launch_bounds__(kCellThreads, 2)
         if (MODE == 1) {
           I_out[(long long)T.h->ext * g.ncell + gc] = I;
         } else {
-          const R w = T.h->w, nx = T.h->n[0], ny = T.h->n[1], nz = T.h->n[2];
-          const R wI = w * I, wIx = wI * nx, wIy = wI * ny, wIz = wI * nz;
-          part[0] += wI;
-          if (kWantF) {
-            part[1] += wIx;
-            part[2] += wIy;
-            part[3] += wIz;
-          }
-          part[4] = fma(wIx, nx, part[4]);
-          part[5] = fma(wIy, ny, part[5]);
-          part[6] = fma(wIz, nz, part[6]);
-          part[7] = fma(wIx, ny, part[7]);
-          part[8] = fma(wIx, nz, part[8]);
-          part[9] = fma(wIy, nz, part[9]);
+          const R *c = T.h->c;  // w (1, n, nn), the same for every lane
+#pragma unroll
+          for (int m = 0; m < 10; ++m)
+            if (kWantF || m == 0 || m >= 4) part[m] = fma(I, c[m], part[m]);
         }
       }
       if (MODE != 1) {
