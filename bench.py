@@ -259,7 +259,7 @@ def learned_measurement(local_rank):
         "network_only": {"ms": t_inf[2], "speedup_vs_plain": plain_ms / t_inf[2], "abs_df_vs_plain": net_err},
         "eddington_I_over_3": {"mean": float(edd.double().mean()), "max": float(edd.max())},
         "conv_roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-                          "frac": tflops / peak, "kernel": "conv3d_kernel (4 layers, mma.sync BF16)",
+                          "frac": tflops / peak, "kernel": "conv3d_tc_kernel (4 layers, tcgen05 BF16, FP32 accumulators in TMEM)",
                           "algorithmic": f"{conv_flops_per_cell()} FLOP per cell (padded channels) x {N} cells"},
         "train": {"snapshots": ntrain, "shape": [nt] * 3, "steps": steps, "batch": batch,
                   "seconds": t_train, "data_seconds": t_data, "final_loss": losses[-1]},

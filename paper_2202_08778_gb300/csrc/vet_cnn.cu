@@ -1,17 +1,16 @@
 // vet_cnn.cu -- kernels of the learned closure (not in the VETTAM paper: a
 // 3D convolutional network predicting the Eddington tensor from local
-// features, with the exact ray tracer as fallback).
+// features, with the exact ray tracer as fallback): features, the weight
+// gradient of the convolutions, head and loss, AdamW, indicator and block
+// list.  The convolutions themselves (forward and data gradient) run on the
+// tcgen05 tensor cores (vet_cnn_tc.cu).
 //
 // Activations are stored cells-major, channels-minor ([volume][z][y][x][C],
-// BF16, C a multiple of 16).  A 3x3x3 convolution with zero padding is an
-// implicit GEMM: M = cells, N = output channels, K = 27 taps x input channels,
-// run on the tensor cores with BF16 mma.sync (m16n8k16, FP32 accumulate).  A
-// CTA keeps a layer's weights in shared memory and loops over output tiles of
-// 8 x 8 x 4 cells, staging each tile's 10 x 10 x 6 input halo.  Rows of both
-// shared arrays are XOR-swizzled in 16-byte chunks so that every ldmatrix
-// phase (8 consecutive rows) touches 8 distinct bank groups.  The same kernel
-// computes the data gradient (a convolution of the output gradient with the
-// flipped, transposed weights); the weight gradient has its own kernel.
+// BF16, C a multiple of 16).  The weight gradient is, per tap, a GEMM with
+// M = output channels, N = input channels and K = the 256 cells of an
+// 8 x 8 x 4 tile, on BF16 mma.sync (m16n8k16, FP32 accumulate) with
+// ldmatrix.trans operands from shared memory whose rows are XOR-swizzled in
+// 16-byte chunks (every ldmatrix phase touches 8 distinct bank groups).
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -101,104 +100,6 @@ __device__ __forceinline__ void load_halo(unsigned char *sm, const __nv_bfloat16
       val = reinterpret_cast<const int4 *>(x + cell * C)[c];
     }
     *reinterpret_cast<int4 *>(sm + swz_off(hc, c, NCH)) = val;
-  }
-}
-
-// ------------------------------------------------------------- convolution
-// out = epi(conv(x, W) [+ b]) with x [vol][C_IN] BF16, W [27][C_OUT][C_IN]
-// BF16 (row = output channel), optional bias b [C_OUT] FP32.
-//   EPI_SILU:     pre = acc + b (stored BF16 if pre_out), out = SiLU(pre) BF16
-//   EPI_F32:      out = acc + b, FP32
-//   EPI_SILU_BWD: out = acc * SiLU'(pre_in) BF16 (data gradient through the
-//                 previous layer's activation), no bias
-template <int C_IN, int C_OUT, int EPI>
-__global__ void __launch_bounds__(kThreads, 2)
-    conv3d_kernel(const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ W,
-                  const float *__restrict__ b, Vol V, __nv_bfloat16 *__restrict__ pre_out,
-                  const __nv_bfloat16 *__restrict__ pre_in, void *__restrict__ out) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int NCI = C_IN / 8, NCO_T = C_OUT / 8, KS = C_IN / 16;
-  unsigned char *sW = smem;                                 // 27 * C_OUT rows of C_IN
-  unsigned char *sX = smem + 27 * C_OUT * C_IN * 2;         // 600 rows of C_IN
-  // weights, once per CTA
-  for (int h = threadIdx.x; h < 27 * C_OUT * NCI; h += blockDim.x) {
-    const int row = h / NCI, c = h - row * NCI;
-    *reinterpret_cast<int4 *>(sW + swz_off(row, c, NCI)) = reinterpret_cast<const int4 *>(W + (long long)row * C_IN)[c];
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t4 = lane & 3;
-  const int wz = warp >> 1, wy = (warp & 1) * 4;  // warp: tile rows y = wy..wy+3 at z = wz
-  const int q = lane >> 3, r8 = lane & 7;
-  const long long vol = (long long)V.nz * V.ny * V.nx;
-  const long long nt = ntiles_of(V);
-  for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const TileIdx ti = tile_of(tile, V);
-    __syncthreads();
-    load_halo<C_IN>(sX, x, V, ti);
-    __syncthreads();
-    float acc[2][NCO_T][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int j = 0; j < NCO_T; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[mt][j][e] = 0.f;
-    for (int tap = 0; tap < 27; ++tap) {
-      const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-#pragma unroll
-      for (int kk = 0; kk < KS; ++kk) {
-        uint32_t a[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          // rows 0-7: y = wy + 2mt, rows 8-15: y + 1; x = row % 8
-          const int y = wy + 2 * mt + (q & 1);
-          const int hc = (wz + 1 + dz) * (HX * HY) + (y + 1 + dy) * HX + (r8 + 1 + dx);
-          ldsm_x4(smem_u32(sX + swz_off(hc, 2 * kk + (q >> 1), NCI)), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
-        }
-#pragma unroll
-        for (int j = 0; j < NCO_T; j += 2) {
-          uint32_t b0, b1, b2, b3;
-          const int row = tap * C_OUT + 8 * (j + (q >> 1)) + r8;
-          ldsm_x4(smem_u32(sW + swz_off(row, 2 * kk + (q & 1), NCI)), b0, b1, b2, b3);
-#pragma unroll
-          for (int mt = 0; mt < 2; ++mt) {
-            mma_bf16(acc[mt][j], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
-            mma_bf16(acc[mt][j + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
-          }
-        }
-      }
-    }
-    // epilogue
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int y = ti.ty * TY + wy + 2 * mt + half, z = ti.tz * TZ + wz, xx = ti.tx * TX + g;
-        if (z >= V.nz || y >= V.ny || xx >= V.nx) continue;
-        const long long cell = (long long)ti.v * vol + ((long long)z * V.ny + y) * V.nx + xx;
-#pragma unroll
-        for (int j = 0; j < NCO_T; ++j) {
-          const int co = 8 * j + 2 * t4;
-          float v0 = acc[mt][j][2 * half], v1 = acc[mt][j][2 * half + 1];
-          if (EPI != EPI_SILU_BWD && b) {
-            v0 += b[co];
-            v1 += b[co + 1];
-          }
-          if (EPI == EPI_F32) {
-            *reinterpret_cast<float2 *>(reinterpret_cast<float *>(out) + cell * C_OUT + co) = make_float2(v0, v1);
-          } else if (EPI == EPI_SILU) {
-            if (pre_out)
-              *reinterpret_cast<__nv_bfloat162 *>(pre_out + cell * C_OUT + co) = __floats2bfloat162_rn(v0, v1);
-            *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(out) + cell * C_OUT + co) =
-                __floats2bfloat162_rn(silu(v0), silu(v1));
-          } else {
-            const __nv_bfloat162 p = *reinterpret_cast<const __nv_bfloat162 *>(pre_in + cell * C_OUT + co);
-            *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(out) + cell * C_OUT + co) =
-                __floats2bfloat162_rn(v0 * silu_grad(__bfloat162float(p.x)), v1 * silu_grad(__bfloat162float(p.y)));
-          }
-        }
-      }
-    }
   }
 }
 
@@ -588,7 +489,6 @@ int grid_for(long long n, int threads) {
 
 }  // namespace
 
-size_t conv_smem_bytes(int cin, int cout) { return (size_t)27 * cout * cin * 2 + (size_t)HN * cin * 2; }
 size_t wgrad_smem_bytes(int cin, int cout) {
   return (size_t)27 * cout * cin * 4 + (size_t)HN * cin * 2 + (size_t)TN * cout * 2;
 }
@@ -610,19 +510,6 @@ int persistent_grid(const void *fn, size_t smem, long long nt, int cap) {
   return (int)g;
 }
 }  // namespace
-
-template <int C_IN, int C_OUT, int EPI>
-cudaError_t conv3d(const __nv_bfloat16 *x, const __nv_bfloat16 *W, const float *b, const Vol &V, __nv_bfloat16 *pre_out,
-                   const __nv_bfloat16 *pre_in, void *out, int grid, cudaStream_t st) {
-  const size_t sm = conv_smem_bytes(C_IN, C_OUT);
-  const void *fn = (const void *)conv3d_kernel<C_IN, C_OUT, EPI>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  const int g = persistent_grid(fn, sm, tiles(V), grid);
-  if (g < 1) return cudaSuccess;
-  conv3d_kernel<C_IN, C_OUT, EPI><<<g, kThreads, sm, st>>>(x, W, b, V, pre_out, pre_in, out);
-  return cudaGetLastError();
-}
 
 template <int C_IN, int C_OUT>
 cudaError_t wgrad(const __nv_bfloat16 *x, const __nv_bfloat16 *gpre, const Vol &V, float *gW, float *gb, int grid,
@@ -689,18 +576,6 @@ cudaError_t unpack_outputs(const float *o, const Vol &V, float *o_out, cudaStrea
   return cudaGetLastError();
 }
 
-template cudaError_t conv3d<16, 32, EPI_SILU>(const __nv_bfloat16 *, const __nv_bfloat16 *, const float *, const Vol &,
-                                              __nv_bfloat16 *, const __nv_bfloat16 *, void *, int, cudaStream_t);
-template cudaError_t conv3d<32, 32, EPI_SILU>(const __nv_bfloat16 *, const __nv_bfloat16 *, const float *, const Vol &,
-                                              __nv_bfloat16 *, const __nv_bfloat16 *, void *, int, cudaStream_t);
-template cudaError_t conv3d<32, 16, EPI_F32>(const __nv_bfloat16 *, const __nv_bfloat16 *, const float *, const Vol &,
-                                             __nv_bfloat16 *, const __nv_bfloat16 *, void *, int, cudaStream_t);
-template cudaError_t conv3d<16, 32, EPI_SILU_BWD>(const __nv_bfloat16 *, const __nv_bfloat16 *, const float *,
-                                                  const Vol &, __nv_bfloat16 *, const __nv_bfloat16 *, void *, int,
-                                                  cudaStream_t);
-template cudaError_t conv3d<32, 32, EPI_SILU_BWD>(const __nv_bfloat16 *, const __nv_bfloat16 *, const float *,
-                                                  const Vol &, __nv_bfloat16 *, const __nv_bfloat16 *, void *, int,
-                                                  cudaStream_t);
 template cudaError_t wgrad<16, 32>(const __nv_bfloat16 *, const __nv_bfloat16 *, const Vol &, float *, float *, int,
                                    cudaStream_t);
 template cudaError_t wgrad<32, 32>(const __nv_bfloat16 *, const __nv_bfloat16 *, const Vol &, float *, float *, int,

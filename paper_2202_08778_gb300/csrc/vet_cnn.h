@@ -28,15 +28,21 @@ struct Vol {
 
 enum { EPI_SILU = 0, EPI_F32 = 1, EPI_SILU_BWD = 2 };
 
-size_t conv_smem_bytes(int cin, int cout);
 size_t wgrad_smem_bytes(int cin, int cout);
 long long tiles(const Vol &V);
 
-// out = epi(conv3d(x, W) + b); see the kernel for the three epilogues.
-// `grid` caps the number of persistent CTAs.
+// out = epi(conv3d(x, W) + b) on the tcgen05 tensor cores (vet_cnn_tc.cu):
+// tiles of 8 x 16 x 2 cells, accumulators in tensor memory.  Epilogues:
+//   EPI_SILU:     pre = acc + b (stored BF16 if pre_out), out = SiLU(pre) BF16
+//   EPI_F32:      out = acc + b, FP32
+//   EPI_SILU_BWD: out = acc * SiLU'(pre_in) BF16 (data gradient through the
+//                 previous layer's activation), no bias
+// A bounded wait that gives up ORs 16 into *status (device) and the kernel
+// returns early.
+size_t conv_tc_smem_bytes(int cin, int cout);
 template <int C_IN, int C_OUT, int EPI>
-cudaError_t conv3d(const __nv_bfloat16 *x, const __nv_bfloat16 *W, const float *b, const Vol &V,
-                   __nv_bfloat16 *pre_out, const __nv_bfloat16 *pre_in, void *out, int grid, cudaStream_t st);
+cudaError_t conv3d_tc(const __nv_bfloat16 *x, const __nv_bfloat16 *W, const float *b, const Vol &V,
+                      __nv_bfloat16 *pre_out, const __nv_bfloat16 *pre_in, void *out, int *status, cudaStream_t st);
 
 // gW[tap][co][ci] += sum_cells gpre[cell][co] x[cell + tap][ci], gb[co] +=
 // sum_cells gpre[cell][co] (FP32, accumulated into the given arrays).

@@ -42,6 +42,7 @@ struct vet_model {
   unsigned int *flags = nullptr;
   int *list = nullptr, *nlist = nullptr;
   int *h_nlist = nullptr;  // pinned
+  int *status = nullptr;   // device: bounded waits of the tensor-core kernels that gave up
   // state of the current batch
   cnn::Vol V{0, 0, 0, 0};
   bool have_features = false, have_forward = false, have_backward = false;
@@ -124,6 +125,7 @@ void free_model(vet_model *m) {
   cudaFree(m->flags);
   cudaFree(m->list);
   cudaFree(m->nlist);
+  cudaFree(m->status);
   cudaFreeHost(m->h_nlist);
   delete m;
 }
@@ -222,10 +224,16 @@ cudaError_t run_forward(vet_model *m, const cnn::Vol &V, bool train, cudaStream_
   using namespace cnn;
   cudaError_t e;
   bf16 *a0 = m->act[0], *a1 = m->act[1], *a2 = train ? m->act[2] : m->act[0];
-  e = conv3d<kInPad, kHidden, EPI_SILU>(m->x0, W(m, 0), bias(m, 0), V, train ? m->pre[0] : nullptr, nullptr, a0, 0, st);
-  if (!e) e = conv3d<kHidden, kHidden, EPI_SILU>(a0, W(m, 1), bias(m, 1), V, train ? m->pre[1] : nullptr, nullptr, a1, 0, st);
-  if (!e) e = conv3d<kHidden, kHidden, EPI_SILU>(a1, W(m, 2), bias(m, 2), V, train ? m->pre[2] : nullptr, nullptr, a2, 0, st);
-  if (!e) e = conv3d<kHidden, kOutPad, EPI_F32>(a2, W(m, 3), bias(m, 3), V, nullptr, nullptr, m->o, 0, st);
+  int *sts = m->status;
+  e = conv3d_tc<kInPad, kHidden, EPI_SILU>(m->x0, W(m, 0), bias(m, 0), V, train ? m->pre[0] : nullptr, nullptr, a0,
+                                          sts, st);
+  if (!e)
+    e = conv3d_tc<kHidden, kHidden, EPI_SILU>(a0, W(m, 1), bias(m, 1), V, train ? m->pre[1] : nullptr, nullptr, a1,
+                                              sts, st);
+  if (!e)
+    e = conv3d_tc<kHidden, kHidden, EPI_SILU>(a1, W(m, 2), bias(m, 2), V, train ? m->pre[2] : nullptr, nullptr, a2,
+                                              sts, st);
+  if (!e) e = conv3d_tc<kHidden, kOutPad, EPI_F32>(a2, W(m, 3), bias(m, 3), V, nullptr, nullptr, m->o, sts, st);
   return e;
 }
 
@@ -280,6 +288,8 @@ VET_API vet_status vet_model_create(vet_model **out, int channels, int device) {
   if (!e) e = cudaMalloc((void **)&m->count, sizeof(unsigned long long));
   if (!e) e = cudaMalloc((void **)&m->loss, sizeof(double));
   if (!e) e = cudaMalloc((void **)&m->nlist, sizeof(int));
+  if (!e) e = cudaMalloc((void **)&m->status, sizeof(int));
+  if (!e) e = cudaMemset(m->status, 0, sizeof(int));
   if (!e) e = cudaMallocHost((void **)&m->h_nlist, sizeof(int));
   for (int i = 0; i < 5 && !e; ++i) e = cudaEventCreate(&m->ev[i]);
   for (float *ptr : {m->p, m->g, m->m, m->v})
@@ -323,12 +333,26 @@ VET_API vet_status vet_model_set_params(vet_model *m, const float *params) {
   return VET_OK;
 }
 
+// Reads and clears the device status word (after a synchronisation).
+static vet_status check_status(vet_model *m) {
+  int sts = 0;
+  cudaError_t e = cudaMemcpy(&sts, m->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) return cuda_fail(m, e, "status read");
+  if (sts) {
+    cudaMemset(m->status, 0, sizeof(int));
+    return fail(m, VET_ETIMEOUT, "a tensor-core wait gave up (status " + std::to_string(sts) + "); outputs are incomplete");
+  }
+  return VET_OK;
+}
+
 static vet_status copy_flat(vet_model *m, const float *src, float *dst) {
   DevGuard dg(m->device);
   std::vector<float> pad((size_t)m->meta.total);
   cudaError_t e = cudaDeviceSynchronize();
   if (!e) e = cudaMemcpy(pad.data(), src, sizeof(float) * pad.size(), cudaMemcpyDeviceToHost);
   if (e) return cuda_fail(m, e, "parameter read");
+  vet_status s = check_status(m);
+  if (s) return s;
   padded_to_host(m, pad, dst);
   return VET_OK;
 }
@@ -397,13 +421,13 @@ VET_API vet_status vet_model_backward(vet_model *m, const float *f_ref, const ui
   if (!e) e = head_loss(m->o, f_ref, mask, V, lam, m->count, m->loss, m->go, st);
   // layer 4: gradient of its output is go
   if (!e) e = wgrad<kHidden, kOutPad>(m->act[2], m->go, V, gW(m, 3), gb(m, 3), 0, st);
-  if (!e) e = conv3d<kOutPad, kHidden, EPI_SILU_BWD>(m->go, Wt(m, 3), nullptr, V, nullptr, m->pre[2], m->g1, 0, st);
+  if (!e) e = conv3d_tc<kOutPad, kHidden, EPI_SILU_BWD>(m->go, Wt(m, 3), nullptr, V, nullptr, m->pre[2], m->g1, m->status, st);
   // layer 3
   if (!e) e = wgrad<kHidden, kHidden>(m->act[1], m->g1, V, gW(m, 2), gb(m, 2), 0, st);
-  if (!e) e = conv3d<kHidden, kHidden, EPI_SILU_BWD>(m->g1, Wt(m, 2), nullptr, V, nullptr, m->pre[1], m->g2, 0, st);
+  if (!e) e = conv3d_tc<kHidden, kHidden, EPI_SILU_BWD>(m->g1, Wt(m, 2), nullptr, V, nullptr, m->pre[1], m->g2, m->status, st);
   // layer 2
   if (!e) e = wgrad<kHidden, kHidden>(m->act[0], m->g2, V, gW(m, 1), gb(m, 1), 0, st);
-  if (!e) e = conv3d<kHidden, kHidden, EPI_SILU_BWD>(m->g2, Wt(m, 1), nullptr, V, nullptr, m->pre[0], m->g1, 0, st);
+  if (!e) e = conv3d_tc<kHidden, kHidden, EPI_SILU_BWD>(m->g2, Wt(m, 1), nullptr, V, nullptr, m->pre[0], m->g1, m->status, st);
   // layer 1 (its input gradient is not needed)
   if (!e) e = wgrad<kInPad, kHidden>(m->x0, m->g1, V, gW(m, 0), gb(m, 0), 0, st);
   if (!e && loss_out) e = cudaMemcpyAsync(loss_out, m->loss, sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -463,6 +487,8 @@ VET_API vet_status vet_closure_learned(vet_ctx *ctx, vet_model *m, const float *
   if (!e) e = cudaEventRecord(m->ev[1], st);
   if (!e) e = cudaStreamSynchronize(st);
   if (e) return cuda_fail(m, e, "learned closure");
+  vet_status s2 = check_status(m);
+  if (s2) return s2;
   // the features, activations and flags of this call replace the training batch's
   m->have_features = m->have_forward = m->have_backward = false;
   m->last_r_cells = cells;
