@@ -135,7 +135,9 @@ vet_status vet_sync(vet_ctx *ctx);
 
 /* Work measure of one closure, from the ray templates: the number of
  * cell-ray segments and face-node-ray segments (one exponential each)
- * summed over all cells, face nodes and directions. */
+ * summed over all cells, face nodes (three downwind faces per block) and
+ * directions.  The face pass skips the downwind faces that lie on the
+ * domain boundary (no block reads them), so it executes a little less. */
 vet_status vet_work_counts(const vet_ctx *ctx, long long *cell_segments, long long *face_segments);
 
 /* Per-phase device timing.  After vet_set_timing(ctx, 1), every vet_trace /

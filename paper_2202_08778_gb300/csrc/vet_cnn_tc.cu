@@ -35,7 +35,6 @@ namespace {
 constexpr int TX = 8, TY = 16, TZ = 2;     // output tile (x, y, z)
 constexpr int HX = 10, HY = 18, HZ = 4;    // input halo
 constexpr int HN = HX * HY * HZ;           // 720 halo cells
-constexpr int kThreads = 256;              // 8 warps: 4 TMEM lane quarters x 2 z-slices
 constexpr long long kWaitPolls = 1LL << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -89,16 +88,6 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return done != 0;
-}
-
-// Bounded wait by a whole warp (all lanes leave together).
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, long long limit) {
-  bool done = false;
-  for (long long i = 0; i < limit; ++i) {
-    if (!done) done = mbar_try(bar, parity);
-    if (__all_sync(0xffffffffu, done)) return true;
-  }
-  return false;
 }
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -168,13 +157,14 @@ __host__ __device__ constexpr size_t halo_bytes() {
   return (size_t)C_IN / 8 * HN * 16;
 }
 
-// Halo of tile ti into one buffer (cp.async, zero outside the volume).
+// Halo of tile ti into one buffer (cp.async, zero outside the volume), by
+// the `nthreads` threads 0 .. nthreads - 1 of the CTA.
 template <int C_IN>
 __device__ __forceinline__ void load_halo(uint32_t dst, const __nv_bfloat16 *__restrict__ x, const Vol &V,
-                                          const Tile &ti) {
+                                          const Tile &ti, int nthreads) {
   constexpr int NCI = C_IN / 8;
   const long long vol = (long long)V.nz * V.ny * V.nx;
-  for (int h = threadIdx.x; h < HN * NCI; h += blockDim.x) {
+  for (int h = threadIdx.x; h < HN * NCI; h += nthreads) {
     const int hc = h / NCI, c = h - hc * NCI;
     const int hz = hc / (HX * HY), hy = (hc / HX) % HY, hx = hc % HX;
     const int z = ti.tz * TZ + hz - 1, y = ti.ty * TY + hy - 1, xx = ti.tx * TX + hx - 1;
@@ -253,18 +243,39 @@ __device__ __forceinline__ void epilogue(uint32_t taddr, const Tile &ti, const V
   for (int i = 0; i < C_OUT / 8; ++i) od[i] = reinterpret_cast<const int4 *>(o2)[i];
 }
 
-// Software pipeline per CTA, iteration i:
-//   1. thread 0 issues the MMAs of tile i (halo buffer i % 2, accumulator
-//      set i % 2) and commits them to bar[i % 2];
-//   2. every warp waits for bar[(i - 1) % 2]: tile i - 1's MMAs are done,
-//      so its halo buffer and accumulators are free to be reused / read;
-//   3. all threads start the cp.async loads of tile i + 1's halo into that
-//      buffer, then
-//   4. read tile i - 1's accumulators and store its outputs;
-//   5. wait for the loads, fence them to the async proxy, barrier.
-// The tensor cores work on tile i while the threads do 3 and 4.
+// Bounded wait on an mbarrier phase by a whole warp, giving up early when
+// another role has aborted (*abort set).
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  bool done = false;
+  for (long long i = 0; i < kWaitPolls; ++i) {
+    if (!done) done = mbar_try(bar, parity);
+    if (__all_sync(0xffffffffu, done)) return true;
+    if ((i & 1023) == 1023 && __any_sync(0xffffffffu, *abort != 0)) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kWorkers = 256;             // warps 0-7: halo loads and epilogue
+constexpr int kTcThreads = kWorkers + 32; // warp 8: issues the MMAs
+
+// Warp-specialised pipeline.  Tile i of this CTA uses halo buffer and
+// accumulator set s = i % 2.
+//   MMA warp (one lane): wait full[s] (halo of tile i landed) and, from
+//     i >= 2, empty[s] (tile i - 2's accumulators read); issue tile i's MMAs;
+//     commit them to done[s].
+//   Workers: wait done[s] (tile i's MMAs finished: buffer s is free, its
+//     accumulators ready); start the cp.async loads of tile i + 2 into buffer
+//     s; read and store tile i's outputs; arrive on empty[s]; complete the
+//     loads, fence them to the async proxy and arrive on full[s].
+// The tensor cores run tile i + 1 while the workers drain tile i and load
+// tile i + 2.  Every wait is bounded; a role that gives up sets `abort`,
+// which ends the other role's waits too.
 template <int C_IN, int C_OUT, int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     conv3d_tc_kernel(const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ W,
                      const float *__restrict__ b, Vol V, __nv_bfloat16 *__restrict__ pre_out,
                      const __nv_bfloat16 *__restrict__ pre_in, void *__restrict__ out, int *status) {
@@ -275,9 +286,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char *sA = smem;                                   // 2 x [NCI][HN][16 B]
   unsigned char *sB = smem + 2 * halo_bytes<C_IN>();          // [27][NCI][C_OUT][16 B]
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t full[2], done[2], empty[2];
   __shared__ uint32_t tmem_base_slot;
-  __shared__ int give_up;
+  __shared__ volatile int abort_flag;
+  __shared__ int n_committed[2];  // MMA batches committed per accumulator set
   __shared__ float sBias[C_OUT];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -288,9 +300,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (threadIdx.x < C_OUT) sBias[threadIdx.x] = b ? b[threadIdx.x] : 0.f;
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    give_up = 0;
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&full[k], kWorkers);
+      mbar_init(&done[k], 1);
+      mbar_init(&empty[k], kWorkers);
+      n_committed[k] = 0;
+    }
+    abort_flag = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
@@ -298,80 +314,93 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  const long long nt = (long long)V.n * ((V.nz + TZ - 1) / TZ) * ((V.ny + TY - 1) / TY) * ((V.nx + TX - 1) / TX);
-  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
-  const uint64_t a_desc0 = smem_desc(a_base, A_LBO, A_SBO);
-  const uint64_t a_desc1 = smem_desc(a_base + (uint32_t)halo_bytes<C_IN>(), A_LBO, A_SBO);
-  const uint64_t b_desc = smem_desc(b_base, B_LBO, B_SBO);
-  long long tile = blockIdx.x;
-  Tile cur = tile_of(tile < nt ? tile : 0, V), prev = cur;
-  if (tile < nt) load_halo<C_IN>(a_base, x, V, cur);
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
   fence_proxy_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = tmem_base_slot;
-  const int sp = warp & 3, zs = warp >> 2;  // TMEM lane quarter and z-slice of this warp
-  const int r = 32 * sp + lane;              // this thread's row of the 128-cell slice
-  uint32_t phase_bits = 0u;     // bit k: phase of bar[k] to wait for next
-  int issued = 0, drained = 0;  // MMA batches committed / completed (thread 0's count is used)
-  bool ok = true;
-  for (int i = 0;; ++i, tile += gridDim.x) {
-    const bool have = tile < nt;
-    const int s = i & 1;
-    if (have && threadIdx.x == 0) {  // 1
-      fence_after_sync();
-      issue_tile<C_IN, C_OUT>(tmem + (uint32_t)(s * 2 * C_OUT), s ? a_desc1 : a_desc0, b_desc);
-      mma_commit(&bar[s]);
-    }
-    if (have) ++issued;
-    if (i > 0) {  // 2: tile i - 1
-      const int p = s ^ 1;
-      if (mbar_wait_warp(&bar[p], (phase_bits >> p) & 1u, kWaitPolls)) {
-        phase_bits ^= 1u << p;
-        ++drained;
-      } else if (lane == 0) {
-        atomicOr(status, 16);
-        give_up = 1;
+  const long long nt = (long long)V.n * ((V.nz + TZ - 1) / TZ) * ((V.ny + TY - 1) / TY) * ((V.nx + TX - 1) / TX);
+  const int ntile = blockIdx.x < nt ? (int)((nt - 1 - blockIdx.x) / gridDim.x + 1) : 0;  // tiles of this CTA
+  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
+
+  if (warp == kWorkers / 32) {
+    // ---- MMA issuer
+    const uint64_t a_desc0 = smem_desc(a_base, A_LBO, A_SBO);
+    const uint64_t a_desc1 = smem_desc(a_base + (uint32_t)halo_bytes<C_IN>(), A_LBO, A_SBO);
+    const uint64_t b_desc = smem_desc(b_base, B_LBO, B_SBO);
+    for (int i = 0; i < ntile; ++i) {
+      const int s = i & 1;
+      const uint32_t use = (uint32_t)(i >> 1);  // this is use number `use` of buffer / accumulator set s
+      bool ok = wait_or_abort(&full[s], use & 1u, &abort_flag);
+      if (ok && i >= 2) ok = wait_or_abort(&empty[s], (use - 1) & 1u, &abort_flag);
+      if (!ok) {
+        if (lane == 0) {
+          atomicOr(status, 16);
+          abort_flag = 1;
+        }
+        break;
       }
-    }
-    __syncthreads();
-    if (give_up) {
-      ok = false;
-      break;
-    }
-    const long long next = tile + gridDim.x;
-    Tile nti = cur;
-    if (have && next < nt) {  // 3
-      nti = tile_of(next, V);
-      load_halo<C_IN>(a_base + (uint32_t)((s ^ 1) * halo_bytes<C_IN>()), x, V, nti);
-    }
-    if (i > 0) {  // 4
       fence_after_sync();
-      epilogue<C_OUT, EPI>(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)((s ^ 1) * 2 * C_OUT + zs * C_OUT), prev, V,
-                           sBias, pre_out, pre_in, out, r, zs);
+      if (lane == 0) {
+        issue_tile<C_IN, C_OUT>(tmem + (uint32_t)(s * 2 * C_OUT), s ? a_desc1 : a_desc0, b_desc);
+        mma_commit(&done[s]);
+        ++n_committed[s];
+      }
+      __syncwarp();
     }
-    if (!have) break;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");  // 5
-    fence_proxy_async();
-    fence_before_sync();
-    __syncthreads();
-    prev = cur;
-    cur = nti;
   }
-  if (!ok && threadIdx.x == 0) {
-    // batches still running: wait for them (bounded) before tensor and
-    // shared memory are released
-    for (int k = drained; k < issued; ++k) {
-      const int p = k & 1;
-      for (long long n = 0; n < kWaitPolls && !mbar_try(&bar[p], (phase_bits >> p) & 1u); ++n) {
+  int n_waited0 = 0, n_waited1 = 0;  // batches this worker saw complete, per set
+  if (warp != kWorkers / 32) {
+    // ---- workers
+    const int sp = warp & 3, zs = warp >> 2;  // TMEM lane quarter and z-slice of this warp
+    const int r = 32 * sp + lane;              // this thread's row of the 128-cell slice
+    // prologue: halos of tiles 0 and 1
+    for (int k = 0; k < 2 && k < ntile; ++k) {
+      load_halo<C_IN>(a_base + (uint32_t)(k * halo_bytes<C_IN>()), x, V,
+                      tile_of(blockIdx.x + (long long)k * gridDim.x, V), kWorkers);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      fence_proxy_async();
+      mbar_arrive(&full[k]);
+    }
+    for (int i = 0; i < ntile; ++i) {
+      const int s = i & 1;
+      const uint32_t use = (uint32_t)(i >> 1);
+      if (!wait_or_abort(&done[s], use & 1u, &abort_flag)) {
+        if (lane == 0) {
+          atomicOr(status, 16);
+          abort_flag = 1;
+        }
+        break;
       }
-      phase_bits ^= 1u << p;
+      if (s) ++n_waited1; else ++n_waited0;
+      fence_after_sync();
+      const bool more = i + 2 < ntile;
+      if (more)
+        load_halo<C_IN>(a_base + (uint32_t)(s * halo_bytes<C_IN>()), x, V,
+                        tile_of(blockIdx.x + (long long)(i + 2) * gridDim.x, V), kWorkers);
+      epilogue<C_OUT, EPI>(tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)(s * 2 * C_OUT + zs * C_OUT),
+                           tile_of(blockIdx.x + (long long)i * gridDim.x, V), V, sBias, pre_out, pre_in, out, r, zs);
+      fence_before_sync();
+      mbar_arrive(&empty[s]);
+      if (more) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        fence_proxy_async();
+        mbar_arrive(&full[s]);
+      }
     }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
   fence_before_sync();
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) {
+    // committed MMAs may still run: wait (bounded) for every batch committed
+    // but not yet seen complete before tensor and shared memory are released
+    for (int k = 0; k < 2; ++k)
+      for (int ph = k ? n_waited1 : n_waited0; ph < n_committed[k]; ++ph)
+        for (long long n = 0; n < kWaitPolls && !mbar_try(&done[k], (uint32_t)ph & 1u); ++n) {
+        }
+  }
   __syncthreads();
   if (warp == 0) {
     fence_after_sync();
@@ -395,12 +424,12 @@ cudaError_t conv3d_tc(const __nv_bfloat16 *x, const __nv_bfloat16 *W, const floa
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, sm) != cudaSuccess || per < 1) per = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTcThreads, sm) != cudaSuccess || per < 1) per = 1;
   // tensor memory: at most 4 CTAs of <= 128 columns share an SM's 512
   if (per > 4) per = 4;
   long long g = (long long)per * sms;
   if (g > nt) g = nt;
-  conv3d_tc_kernel<C_IN, C_OUT, EPI><<<(int)g, kThreads, sm, st>>>(x, W, b, V, pre_out, pre_in, out, status);
+  conv3d_tc_kernel<C_IN, C_OUT, EPI><<<(int)g, kTcThreads, sm, st>>>(x, W, b, V, pre_out, pre_in, out, status);
   return cudaGetLastError();
 }
 

@@ -76,7 +76,7 @@ inline void merge_events(Event *ev, int n) {
 // block's cell rays and face-node rays cross for this direction.
 template <typename R>
 void build_template(const double *d, int ext, int B, double h, unsigned char *out, long long &cell_segs,
-                    long long &node_segs) {
+                    long long node_segs[3]) {
   const TplLayout L = tpl_layout<R>(B);
   std::memset(out, 0, L.bytes);
   auto *hd = reinterpret_cast<TplHead<R> *>(out);
@@ -174,7 +174,7 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   fill_exit(ck, cw, B, true);
   fill_exit(nk, nw, B + 1, false);
   // work measure: segments = exit event index + 1 per ray
-  long long cs = 0, ns = 0;
+  long long cs = 0, ns[3] = {0, 0, 0};
   for (int l2 = 0; l2 < B; ++l2)
     for (int l1 = 0; l1 < B; ++l1)
       for (int l0 = 0; l0 < B; ++l0)
@@ -189,11 +189,11 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
         P[c] = v;
         int Lq[3];
         for (int q = 0; q < 3; ++q) Lq[q] = sgn[q] > 0 ? P[q] : B - P[q];
-        ns += 1 + std::min({(int)npos[Lq[0]], (int)npos[(B + 1) + Lq[1]], (int)npos[2 * (B + 1) + Lq[2]]});
+        ns[a] += 1 + std::min({(int)npos[Lq[0]], (int)npos[(B + 1) + Lq[1]], (int)npos[2 * (B + 1) + Lq[2]]});
       }
   }
   cell_segs = cs;
-  node_segs = ns;
+  for (int a = 0; a < 3; ++a) node_segs[a] = ns[a];
 }
 
 inline int octant_of(const double *d) { return (d[0] < 0) + 2 * (d[1] < 0) + 4 * (d[2] < 0); }
@@ -234,9 +234,14 @@ inline long long build_schedule(const int nb[3], const int ob[9], int group, Fac
         for (int by = 0; by < nb[1]; ++by)
           for (int bx = 0; bx < nb[0]; ++bx) {
             const int bb[3] = {bx, by, bz};
-            int lv = 0;
-            for (int a = 0; a < 3; ++a) lv += s[a] > 0 ? bb[a] : nb[a] - 1 - bb[a];
-            if (lv != L) continue;
+            int lv = 0, live = 0;
+            for (int a = 0; a < 3; ++a) {
+              lv += s[a] > 0 ? bb[a] : nb[a] - 1 - bb[a];
+              live += (s[a] > 0 ? bb[a] + 1 < nb[a] : bb[a] > 0) ? 1 : 0;  // downwind neighbour exists
+            }
+            // a block whose downwind faces all lie on the domain boundary
+            // produces nothing any block reads
+            if (lv != L || live == 0) continue;
             const int id = (bz * nb[1] + by) * nb[0] + bx;
             for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += group) f(id, d0, std::min(group, ob[o + 1] - d0));
           }

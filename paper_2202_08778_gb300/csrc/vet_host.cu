@@ -131,12 +131,14 @@ vet_status build_context(vet_ctx *c) {
   std::vector<unsigned char> tpl((size_t)tbytes * N);
   long long cs_tot = 0, ns_tot = 0;
   for (int i = 0; i < N; ++i) {
-    long long cs, ns;
+    long long cs, ns[3];
     vet::geom::build_template<R>(&c->dirs_ext[4 * order[i]], order[i], B, c->grid.h, tpl.data() + (size_t)i * tbytes,
                                  cs, ns);
     cs_tot += cs;
-    ns_tot += ns;
+    ns_tot += ns[0] + ns[1] + ns[2];
   }
+  // the method's work: every block's three downwind faces (the face pass
+  // skips those on the domain boundary, which no block reads)
   c->cell_segs = cs_tot * c->nblk;
   c->face_segs = ns_tot * c->nblk;
   std::memcpy(c->ob, ob, sizeof ob);

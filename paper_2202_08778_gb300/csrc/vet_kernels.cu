@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full;
   const int B = BC ? BC : g.B;
-  const int W = B + 2, N1 = B + 1, NN = N1 * N1, NN3 = 3 * NN;
+  const int W = B + 2, N1 = B + 1, NN = N1 * N1;
   const TileShape ts = node_tile(B);
   const TplLayout TL = tpl_layout<R>(B);
   const size_t sb = slot_bytes<R>(B);
@@ -309,11 +309,26 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     if (threadIdx.x == 0) mbar_wait(&full, 0, kDrainPolls, status, 8);
     return;
   }
-  for (int w = threadIdx.x; w < it.dir_count * NN3; w += blockDim.x) {
-    const int j = w / NN3, n = w - j * NN3;
+  // Downwind faces on the domain boundary are read by no block: only the
+  // axes whose downwind neighbour exists are computed (the directions of an
+  // item share one octant, hence one set of axes).
+  int live = 0, nlive = 0;  // live: the computed axes, 2 bits each
+  {
+    const TplHead<R> *h0 = reinterpret_cast<const TplHead<R> *>(slots);
+    const int bb[3] = {bx, by, bz}, nbb[3] = {g.nbx, g.nby, g.nbz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int nb = bb[a] + h0->sgn[a];
+      if (nb >= 0 && nb < nbb[a]) live |= a << (2 * nlive++);
+    }
+  }
+  const int NNL = nlive * NN;
+  for (int w = threadIdx.x; w < it.dir_count * NNL; w += blockDim.x) {
+    const int j = w / NNL, n = w - j * NNL;
     const Tpl<R> T(slots + sb * j, TL);
     const R *fin = reinterpret_cast<const R *>(slots + sb * j + TL.bytes);
-    const int a = n / NN, r = n - a * NN;
+    const int ai = n / NN, r = n - ai * NN;
+    const int a = (live >> (2 * ai)) & 3;
     const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
     // upwind-frame node coordinates (L0, L1, L2): B along the face's axis
     const int L0 = a == 0 ? B : ub;

@@ -121,7 +121,7 @@ VET_API vet_status vet_closure_noalloc(const vet_grid *grid, const vet_config *c
   int ob[9];
   vet::geom::internal_order(N, h_dirs, h_order, ob);
   for (int i = 0; i < N; ++i) {
-    long long cs, ns;
+    long long cs, ns[3];
     vet::geom::build_template<float>(h_dirs + 4 * h_order[i], h_order[i], B, g.h, h_tpl + (size_t)i * tbytes, cs,
                                      ns);
   }
