@@ -218,6 +218,45 @@ inline void interleaved_order(const int ob[9], int *out) {
       if (ob[o] + r < ob[o + 1]) out[n++] = ob[o] + r;
 }
 
+// Cell order of antipodal pairs: for every internal direction i the
+// internal index of -n_i (components equal and opposite within 1e-12), the
+// pair listed as (d, -d) with d the member whose first nonzero component is
+// positive, pairs in increasing order of d.  Returns false (out untouched)
+// when some direction has no antipode in the set.
+inline bool antipodal_order(int N, const double *dirs, const int *order, int *out) {
+  int *mate = new int[N];
+  for (int i = 0; i < N; ++i) mate[i] = -1;
+  bool ok = true;
+  for (int i = 0; i < N && ok; ++i) {
+    if (mate[i] >= 0) continue;
+    const double *a = dirs + 4 * order[i];
+    for (int j = 0; j < N; ++j) {
+      if (j == i || mate[j] >= 0) continue;
+      const double *b = dirs + 4 * order[j];
+      if (std::fabs(a[0] + b[0]) < 1e-12 && std::fabs(a[1] + b[1]) < 1e-12 && std::fabs(a[2] + b[2]) < 1e-12) {
+        mate[i] = j;
+        mate[j] = i;
+        break;
+      }
+    }
+    ok = mate[i] >= 0;
+  }
+  if (ok) {
+    int n = 0;
+    for (int i = 0; i < N; ++i) {
+      const double *a = dirs + 4 * order[i];
+      const double lead = a[0] != 0.0 ? a[0] : (a[1] != 0.0 ? a[1] : a[2]);
+      if (lead > 0.0) {
+        out[n++] = i;
+        out[n++] = mate[i];
+      }
+    }
+    ok = n == N;
+  }
+  delete[] mate;
+  return ok;
+}
+
 // Face-pass schedule: level L of block b in octant o is b's upwind-ordered
 // index sum; one item = (block, up to `group` directions of one octant).
 // Writes level_off[0..nlevels] and, when items != nullptr, the items.

@@ -144,6 +144,12 @@ vet_status build_context(vet_ctx *c) {
   std::memcpy(c->ob, ob, sizeof ob);
   std::vector<int> cell_order(N);
   vet::geom::interleaved_order(ob, cell_order.data());
+  // FP32 cell pass on mirrored ray pairs where the set is closed under
+  // negation (block edges 8 and 16)
+  c->dims.paired = 0;
+  if (!c->fp64 && (B == 8 || B == 16) && vet::geom::antipodal_order(N, c->dirs_ext.data(), order.data(),
+                                                                     cell_order.data()))
+    c->dims.paired = 1;
   // moment coefficients in HEALPix order
   std::vector<R> coef((size_t)N * 10);
   for (int k = 0; k < N; ++k) {

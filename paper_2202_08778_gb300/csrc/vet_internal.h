@@ -97,6 +97,7 @@ struct GridDims {
   int ndir;           // directions
   long long ncell;    // nx*ny*nz
   int dir_tile;       // directions per cell-pass tile (0: default)
+  int paired;         // 1: the cell order lists antipodal pairs (d, -d), see the paired cell pass
 };
 
 // Shared-memory kappa/S tiles of a block.  Face pass: cell (x, y, z) at

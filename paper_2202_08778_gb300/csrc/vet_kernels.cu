@@ -277,6 +277,16 @@ constexpr int kFaceThreads = 512;
 // of the item's templates and incoming faces, all in flight at once, while
 // the CTA loads the block's kappa/S tile; then the (direction, node) rays are
 // spread over the threads.
+// Directions per tile of the paired cell pass: an even number (whole pairs)
+// whose two buffers fit, at most the tuned tile rounded up to even.
+inline int pair_dir_tile(int B, int want) {
+  int dt = want > 0 ? want : kDirTile;
+  dt = (dt + 1) & ~1;
+  if (dt > kMaxTune) dt = kMaxTune;
+  while (dt > 2 && smem_bytes<float>(B, 2 * dt) > kSmemMax) dt -= 2;
+  return dt;
+}
+
 template <typename R, int BC>
 __global__ void __launch_bounds__(kFaceThreads, 2)
     face_pass_kernel(GridDims g, const R *__restrict__ kappa, const R *__restrict__ S,
@@ -532,6 +542,254 @@ __global__ void __launch_bounds__(kCellThreads, 2)
   }
 }
 
+// --------------------------------------------- cell pass, mirrored ray pairs
+// FP32 cell pass for block edges 8 and 16 and direction sets closed under
+// negation (HEALPix sets are, rotated or not).  The ray from cell c in
+// direction d and the ray from the point-mirrored cell c' = (B-1-x, B-1-y,
+// B-1-z) in direction -d are mirror images (and so are (c, -d) and (c', d)):
+// in their own upwind frames both
+// start at the same coordinates along every axis the direction crosses, leave
+// through the same event with the same exit-table entries, and cross segments
+// of the same lengths whose tile offsets are negatives of each other.  So one
+// thread marches both in lockstep from one event list, with the two
+// exponentials' arithmetic on packed FP32 pairs (f32x2), and only the
+// in-plane face coordinates (which may differ along an axis the direction
+// does not cross) and the staged faces are per ray.  The cell order lists
+// the pairs (d, -d) consecutively; a staged tile holds dt / 2 pairs.
+constexpr int kPairThreads = 256;  // one lower-half cell and its mirror per thread
+
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+  return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ void upk2(uint64_t r, float &a, float &b) {
+  a = __uint_as_float((uint32_t)r);
+  b = __uint_as_float((uint32_t)(r >> 32));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// One segment of both rays: t1, t2 are the byte addresses of the rays' start
+// cells in the (kappa, S) tile; the mirror ray moves by -off.  The same update
+// and the same two forms as segment().
+__device__ __forceinline__ void segment_pair(const unsigned char *__restrict__ t1, const unsigned char *__restrict__ t2,
+                                             const TplEvent<float> &ev, uint64_t &I) {
+  const float k1 = *reinterpret_cast<const float *>(t1 + ev.off);
+  const float s1 = *reinterpret_cast<const float *>(t1 + ev.off + 4);
+  const float k2 = *reinterpret_cast<const float *>(t2 - ev.off);
+  const float s2 = *reinterpret_cast<const float *>(t2 - ev.off + 4);
+  const uint64_t Y = mul2(pk2(k1, k2), pk2(ev.len, ev.len));
+  float y1, y2;
+  upk2(Y, y1, y2);
+  float e1, e2;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(y1));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(y2));
+  uint64_t q = pk2(1.0833843353054956e-03f, 1.0833843353054956e-03f);
+  q = fma2(q, Y, pk2(9.4645342235962007e-03f, 9.4645342235962007e-03f));
+  q = fma2(q, Y, pk2(5.5464640186780434e-02f, 5.5464640186780434e-02f));
+  q = fma2(q, Y, pk2(2.4022290282685121e-01f, 2.4022290282685121e-01f));
+  q = fma2(q, Y, pk2(6.9314712699664371e-01f, 6.9314712699664371e-01f));
+  float n1, n2;  // -(1 - e^-x) of the thin form
+  upk2(mul2(q, Y), n1, n2);
+  const bool thin1 = y1 > -0.7213475204444817f, thin2 = y2 > -0.7213475204444817f;
+  float i1, i2;
+  upk2(I, i1, i2);
+  I = fma2(sub2(I, pk2(s1, s2)), pk2(thin1 ? n1 : e1, thin2 ? n2 : e2), pk2(thin1 ? i1 : s1, thin2 ? i2 : s2));
+}
+
+template <int MODE, int BC>
+__global__ void __launch_bounds__(kPairThreads, 2)
+    cell_pair_kernel(GridDims g, int parts, int dt, const float *__restrict__ kappa, const float *__restrict__ S,
+                     const unsigned char *__restrict__ tpl_g, const int *__restrict__ order,
+                     const float *__restrict__ faces, const float *__restrict__ bnd, float *__restrict__ I_out,
+                     float *__restrict__ M_out, float *__restrict__ E_out, float *__restrict__ f_out, void *emax_bits,
+                     long long spin_limit, int *status, const int *__restrict__ block_list) {
+  constexpr int B = BC, B2 = B * B;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[2], empty[2];
+  const TileShape ts = cell_tile(B);
+  const TplLayout TL = tpl_layout<float>(B);
+  const int fstride = g.fstride;
+  const size_t sb = slot_bytes<float>(B);
+  float2 *tile = reinterpret_cast<float2 *>(smem);
+  unsigned char *buf0 = smem + align16(sizeof(float2) * (size_t)ts.elems);
+  const int item = blockIdx.x / parts, part = blockIdx.x - item * parts;
+  const int blk = block_list ? block_list[item] : item;
+  const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
+  const int nwarps = blockDim.x >> 5;
+  const int ntiles = (g.ndir + dt - 1) / dt;
+  int issued = 0, consumed = 0;
+  auto issue_tile = [&](int t) {  // thread 0 only
+    issued = t + 1;
+    const int b = t & 1, d0 = t * dt, nd = min(dt, g.ndir - d0);
+    unsigned char *buf = buf0 + (size_t)b * dt * sb;
+    mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
+    for (int j = 0; j < nd; ++j)
+      issue_slot<float>(buf + sb * j, g, TL, bx, by, bz, order[d0 + j], tpl_g, faces, bnd, &full[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], nwarps);
+    mbar_init(&empty[1], nwarps);
+    mbar_fence_init();
+    issue_tile(0);
+    if (ntiles > 1) issue_tile(1);
+  }
+  load_tile<float, BC>(tile, ts, g, bx, by, bz, kappa, S);
+  __syncthreads();
+
+  // this thread's lower-half cell (z < B/2): 4 x 4 x 2 bricks, warp-major
+  const int q = part * kPairThreads + (int)threadIdx.x;
+  const int qb = q >> 5, ln = q & 31;
+  const int cx = 4 * (qb % (B / 4)) + (ln & 3);
+  const int cy = 4 * ((qb / (B / 4)) % (B / 4)) + ((ln >> 2) & 3);
+  const int cz = 2 * (qb / (B2 / 16)) + (ln >> 4);
+  const int mx = B - 1 - cx, my = B - 1 - cy, mz = B - 1 - cz;  // the mirror cell
+  const unsigned char *t1 = reinterpret_cast<const unsigned char *>(tile + (cx + ts.sy * cy + ts.sz * cz));
+  const unsigned char *t2 = reinterpret_cast<const unsigned char *>(tile + (mx + ts.sy * my + ts.sz * mz));
+  const long long gc1 = ((long long)(bz * B + cz) * g.ny + (by * B + cy)) * g.nx + (bx * B + cx);
+  const long long gc2 = ((long long)(bz * B + mz) * g.ny + (by * B + my)) * g.nx + (bx * B + mx);
+  constexpr bool kWantF = MODE == 0;
+  float mom[2][10], cmp[2][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+#pragma unroll
+    for (int m = 0; m < 10; ++m) mom[r][m] = 0.f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) cmp[r][m] = 0.f;
+  }
+
+  bool ok = true;
+  for (int t = 0; t < ntiles && ok; ++t) {
+    const int b = t & 1;
+    const uint32_t ph = (uint32_t)((t >> 1) & 1);
+    if (!mbar_wait_warp(&full[b], ph, spin_limit, status, 2)) { ok = false; break; }
+    consumed = t + 1;
+    const int nd = min(dt, g.ndir - t * dt);
+    const unsigned char *buf = buf0 + (size_t)b * dt * sb;
+    float part_[2][10];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int m = 0; m < 10; ++m) part_[r][m] = 0.f;
+    // every cell needs both members of a pair: (c, d) with (c', -d), then
+    // (c, -d) with (c', d), the primary direction's template driving each
+    for (int jj = 0; jj < nd; ++jj) {
+      const int j = (jj >> 1) << 1, j1 = j + (jj & 1), j2 = j + 1 - (jj & 1);
+      const Tpl<float> T(buf + sb * j1, TL);  // primary: events and tables
+      const TplHead<float> *H2 = reinterpret_cast<const TplHead<float> *>(buf + sb * j2);  // its antipode
+      const float *fin1 = reinterpret_cast<const float *>(buf + sb * j1 + TL.bytes);
+      const float *fin2 = reinterpret_cast<const float *>(buf + sb * j2 + TL.bytes);
+      const int l0 = T.h->sgn[0] > 0 ? cx : B - 1 - cx;
+      const int l1 = T.h->sgn[1] > 0 ? cy : B - 1 - cy;
+      const int l2 = T.h->sgn[2] > 0 ? cz : B - 1 - cz;
+      const int m0 = H2->sgn[0] > 0 ? mx : B - 1 - mx;
+      const int m1 = H2->sgn[1] > 0 ? my : B - 1 - my;
+      const int m2 = H2->sgn[2] > 0 ? mz : B - 1 - mz;
+      const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
+      int last = p0, ae = 0, la = l0, lb = l1, lc = l2, nb_ = m1, nc_ = m2;
+      if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; nb_ = m0; }
+      if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; nb_ = m0; nc_ = m1; }
+      const int row = (ae * 2) * B + la;
+      const int kb = T.ck[row], kc = T.ck[row + B];
+      const float2 wb = T.cw[row], wc = T.cw[row + B];
+      const float Iin1 = face_value<float>(fin1, fstride, B, ae, lb, lc, kb, kc, wb, wc);
+      const float Iin2 = face_value<float>(fin2, fstride, B, ae, nb_, nc_, kb, kc, wb, wc);
+      uint64_t I = pk2(Iin1, Iin2);
+      int e = last;
+      for (; e > 0; e -= 2) {
+        const TplEvent<float> e0 = T.cev[e], e1 = T.cev[e - 1];
+        segment_pair(t1, t2, e0, I);
+        segment_pair(t1, t2, e1, I);
+      }
+      if (e == 0) segment_pair(t1, t2, T.cev[0], I);
+      float I1, I2;
+      upk2(I, I1, I2);
+      if (MODE == 1) {
+        I_out[(long long)T.h->ext * g.ncell + gc1] = I1;
+        I_out[(long long)H2->ext * g.ncell + gc2] = I2;
+      } else {
+        const float *c1 = T.h->c, *c2 = H2->c;
+#pragma unroll
+        for (int m = 0; m < 10; ++m)
+          if (kWantF || m == 0 || m >= 4) {
+            part_[0][m] = fmaf(I1, c1[m], part_[0][m]);
+            part_[1][m] = fmaf(I2, c2[m], part_[1][m]);
+          }
+      }
+    }
+    if (MODE != 1) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {  // E, Pxx, Pyy, Pzz: compensated fold
+          const int m = qq == 0 ? 0 : 3 + qq;
+          const float y = part_[r][m] - cmp[r][qq];
+          const float tt = mom[r][m] + y;
+          cmp[r][qq] = (tt - mom[r][m]) - y;
+          mom[r][m] = tt;
+        }
+        if (kWantF) {
+          mom[r][1] += part_[r][1];
+          mom[r][2] += part_[r][2];
+          mom[r][3] += part_[r][3];
+        }
+        mom[r][7] += part_[r][7];
+        mom[r][8] += part_[r][8];
+        mom[r][9] += part_[r][9];
+      }
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[b]);
+    bool prod_ok = true;
+    if (threadIdx.x == 0 && t + 2 < ntiles) {
+      prod_ok = mbar_wait(&empty[b], ph, spin_limit, status, 4);
+      if (prod_ok) issue_tile(t + 2);
+    }
+    if (!__shfl_sync(0xffffffffu, prod_ok ? 1 : 0, 0)) { ok = false; break; }
+  }
+  if (threadIdx.x == 0) {
+    for (int t = consumed; t < issued; ++t) mbar_wait(&full[t & 1], (uint32_t)((t >> 1) & 1), kDrainPolls, status, 8);
+  }
+  if (MODE != 1) {
+    float emax = 0.f;
+    if (ok) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const long long gc = r ? gc2 : gc1;
+        const float E = mom[r][0];
+        if (kWantF) {
+          for (int m = 0; m < 10; ++m) M_out[m * g.ncell + gc] = mom[r][m];
+        } else {
+          E_out[gc] = E;
+        }
+        if (E > 0.f) {
+          const float inv = 1.f / E;
+          for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = mom[r][4 + m] * inv;
+        } else {
+          for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = m < 3 ? 1.f / 3.f : 0.f;
+        }
+        emax = fmaxf(emax, E);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(emax_bits, emax);
+  }
+}
+
 // Boundary faces of every direction, materialised so that staging is a
 // plain bulk copy: bnd[face][d][i] = Ib[face][ext(d)] (0 for vacuum).
 template <typename R>
@@ -632,6 +890,18 @@ void cell_launch(const GridDims &g, const R *kappa, const R *S, const unsigned c
       block_list);
 }
 
+template <int MODE, int BC>
+void pair_launch(const GridDims &g, const float *kappa, const float *S, const unsigned char *tpl, const int *order,
+                 const float *faces, const float *bnd, float *I_out, float *M_out, float *E_out, float *f_out,
+                 void *emax_bits, long long spin, int *status, const int *block_list, int nlist, cudaStream_t st) {
+  const int parts = BC * BC * BC / 2 / kPairThreads;
+  const int nblk = block_list ? nlist : g.nbx * g.nby * g.nbz;
+  const int dt = pair_dir_tile(BC, g.dir_tile);
+  cell_pair_kernel<MODE, BC><<<nblk * parts, kPairThreads, smem_bytes<float>(BC, 2 * dt), st>>>(
+      g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, status,
+      block_list);
+}
+
 template <typename R>
 cudaError_t set_smem_attrs() {
   const int lim = (int)kSmemMax;
@@ -642,6 +912,13 @@ cudaError_t set_smem_attrs() {
                        (const void *)cell_pass_kernel<R, 1, 0>,    (const void *)cell_pass_kernel<R, 2, 8>,
                        (const void *)cell_pass_kernel<R, 2, 16>,   (const void *)cell_pass_kernel<R, 2, 0>};
   for (const void *f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+  }
+  const void *pfns[] = {(const void *)cell_pair_kernel<0, 8>,  (const void *)cell_pair_kernel<0, 16>,
+                        (const void *)cell_pair_kernel<1, 8>,  (const void *)cell_pair_kernel<1, 16>,
+                        (const void *)cell_pair_kernel<2, 8>,  (const void *)cell_pair_kernel<2, 16>};
+  for (const void *f : pfns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
   }
@@ -667,6 +944,28 @@ cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const 
                              R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st,
                              const int *block_list, int nlist) {
   if (block_list && nlist <= 0) return cudaSuccess;
+  if constexpr (sizeof(R) == sizeof(float)) {
+    if (g.paired && (g.B == 16 || g.B == 8)) {
+      const float *k = reinterpret_cast<const float *>(kappa), *s = reinterpret_cast<const float *>(S);
+      const float *fc = reinterpret_cast<const float *>(faces), *bd = reinterpret_cast<const float *>(bnd);
+      float *Io = reinterpret_cast<float *>(I_out), *Mo = reinterpret_cast<float *>(M_out);
+      float *Eo = reinterpret_cast<float *>(E_out), *fo = reinterpret_cast<float *>(f_out);
+      const int mode2 = mode == 0 ? (M_out ? 0 : 2) : 1;
+#define VET_PAIR(MODE, BC) \
+  pair_launch<MODE, BC>(g, k, s, tpl, order, fc, bd, Io, Mo, Eo, fo, emax_bits, spin, status, block_list, nlist, st)
+      if (g.B == 16) {
+        if (mode2 == 0) VET_PAIR(0, 16);
+        else if (mode2 == 2) VET_PAIR(2, 16);
+        else VET_PAIR(1, 16);
+      } else {
+        if (mode2 == 0) VET_PAIR(0, 8);
+        else if (mode2 == 2) VET_PAIR(2, 8);
+        else VET_PAIR(1, 8);
+      }
+#undef VET_PAIR
+      return cudaGetLastError();
+    }
+  }
 #define VET_CELL(MODE, BC)                                                                                  \
   cell_launch<R, MODE, BC>(g, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, \
                            status, block_list, nlist, st)
