@@ -610,7 +610,7 @@ __device__ __forceinline__ void segment_pair(const unsigned char *__restrict__ t
 }
 
 template <int MODE, int BC>
-__global__ void __launch_bounds__(kPairThreads, 2)
+__global__ void __launch_bounds__(kPairThreads, 3)
     cell_pair_kernel(GridDims g, int parts, int dt, const float *__restrict__ kappa, const float *__restrict__ S,
                      const unsigned char *__restrict__ tpl_g, const int *__restrict__ order,
                      const float *__restrict__ faces, const float *__restrict__ bnd, float *__restrict__ I_out,
