@@ -365,7 +365,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = cell_segs / (cell_ms * 1e-3) / 1e9
     traffic = measured_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G exp/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "cell_pass_kernel<float,2,16>",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "cell_pair_kernel<2,16> (FP32 cell pass on mirrored ray pairs)",
                 "peak_basis": f"MUFU ex2: {MUFU_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {sm_max:.0f} MHz",
                 "algorithmic": f"{cell_segs} cell-ray segments (one exp each) per launch"}
 

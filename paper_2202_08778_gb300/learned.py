@@ -80,3 +80,43 @@ def train(model, data, shape, B: int, h: float, steps: int, batch: int = 4, lr_m
         if (log_every and it % log_every == 0) or it == steps - 1:
             losses.append(float(loss.item()))
     return losses
+
+
+def main(argv=None):
+    """Run the learned closure (network only, no fallback) on a seeded n^3
+    lognormal field after the exact closure that supplies E, and print the
+    device timings.  The network is untrained (He initialisation, small random
+    last layer): this measures cost, not accuracy."""
+    import argparse
+
+    import torch
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--block", type=int, default=16)
+    ap.add_argument("--nside", type=int, default=4)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--repeat", type=int, default=3)
+    a = ap.parse_args(argv)
+    p = synth.lognormal_problem(n=a.n, B=a.block, nside=a.nside, seed=a.seed)
+    ctx = vet.Context(p["kappa"].shape, a.block, p["h"], a.nside, p["q"])
+    k = torch.from_numpy(np.ascontiguousarray(p["kappa"].astype(np.float32))).cuda()
+    S = torch.from_numpy(np.ascontiguousarray(p["S"].astype(np.float32))).cuda()
+    N = a.n ** 3
+    f = torch.empty(6 * N, device="cuda")
+    M = torch.empty(10 * N, device="cuda")
+    ctx.closure(k, S, None, f, M)
+    ctx.sync()
+    E = M[:N].clone()
+    model = vet.Model()
+    params = init_params(32, seed=0)
+    W3, b3 = params[-1]
+    params[-1] = (np.random.default_rng(0).uniform(-0.05, 0.05, W3.shape), b3)
+    model.set_params(params)
+    for _ in range(a.repeat):
+        model.closure(ctx, k, S, E, f, threshold=float("inf"))
+        print("learned closure ms (network, fallback, total, convolutions):", model.last_timing())
+
+
+if __name__ == "__main__":
+    main()
