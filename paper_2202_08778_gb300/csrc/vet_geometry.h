@@ -257,6 +257,35 @@ inline bool antipodal_order(int N, const double *dirs, const int *order, int *ou
   return ok;
 }
 
+// Whether the cell-ray parts of two templates (of antipodal directions) are
+// exact mirror images: equal event lengths (relative 1e-6) with negated
+// offsets, zero-length tie segments aside, and identical exit-event and
+// exit tables.  Near-ties of plane crossings (|n_a| equal to the last bit, as on
+// the unrotated HEALPix rings at 45 degrees) can be ordered differently for
+// a direction and its antipode; such pairs fail the test.
+template <typename R>
+inline bool mirror_templates(const unsigned char *ta, const unsigned char *tb, int B) {
+  const TplLayout L = tpl_layout<R>(B);
+  const TplEvent<R> *ea = reinterpret_cast<const TplEvent<R> *>(ta + L.cev);
+  const TplEvent<R> *eb = reinterpret_cast<const TplEvent<R> *>(tb + L.cev);
+  double scale = 0.0;
+  for (int e = 0; e < 3 * B; ++e) scale = std::max(scale, std::fabs((double)ea[e].len));
+  for (int e = 0; e < 3 * B; ++e) {
+    const double la = ea[e].len, lb = eb[e].len;
+    // zero-length segments between tied interior crossings may sit in
+    // either neighbouring cell: they change nothing
+    if (std::fabs(la) <= 1e-9 * scale && std::fabs(lb) <= 1e-9 * scale) continue;
+    if (ea[e].off != -eb[e].off) return false;
+    if (std::fabs(la - lb) > 1e-6 * std::fabs(la)) return false;
+  }
+  if (std::memcmp(ta + L.cpos, tb + L.cpos, 3 * B * 2) != 0) return false;
+  if (std::memcmp(ta + L.ck, tb + L.ck, 6 * B * 2) != 0) return false;
+  const R *wa = reinterpret_cast<const R *>(ta + L.cw), *wb = reinterpret_cast<const R *>(tb + L.cw);
+  for (int i = 0; i < 6 * B * 2; ++i)
+    if (std::fabs((double)wa[i] - (double)wb[i]) > 1e-6) return false;
+  return true;
+}
+
 // Face-pass schedule: level L of block b in octant o is b's upwind-ordered
 // index sum; one item = (block, up to `group` directions of one octant).
 // Writes level_off[0..nlevels] and, when items != nullptr, the items.

@@ -148,8 +148,17 @@ vet_status build_context(vet_ctx *c) {
   // negation (block edges 8 and 16)
   c->dims.paired = 0;
   if (!c->fp64 && (B == 8 || B == 16) && vet::geom::antipodal_order(N, c->dirs_ext.data(), order.data(),
-                                                                     cell_order.data()))
+                                                                     cell_order.data())) {
     c->dims.paired = 1;
+    // pairs whose templates are not exact mirrors are marched ray by ray
+    for (int k = 0; k < N; k += 2) {
+      unsigned char *ta = tpl.data() + (size_t)cell_order[k] * tbytes;
+      unsigned char *tb = tpl.data() + (size_t)cell_order[k + 1] * tbytes;
+      const int m = vet::geom::mirror_templates<R>(ta, tb, B) ? 1 : 0;
+      reinterpret_cast<vet::TplHead<R> *>(ta)->mirror = m;
+      reinterpret_cast<vet::TplHead<R> *>(tb)->mirror = m;
+    }
+  }
   // moment coefficients in HEALPix order
   std::vector<R> coef((size_t)N * 10);
   for (int k = 0; k < N; ++k) {

@@ -609,6 +609,21 @@ __device__ __forceinline__ void segment_pair(const unsigned char *__restrict__ t
   I = fma2(sub2(I, pk2(s1, s2)), pk2(thin1 ? n1 : e1, thin2 ? n2 : e2), pk2(thin1 ? i1 : s1, thin2 ? i2 : s2));
 }
 
+// One cell ray on its own template (upwind-frame coordinates l0..l2, start
+// cell at byte address tb in the tile): exit lookup, entry value, march.
+template <typename R>
+__device__ __forceinline__ R cell_ray(const Tpl<R> &T, const R *fin, int fstride, int B, int l0, int l1, int l2,
+                                      const vec2_t<R> *tile, const unsigned char *tb) {
+  const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
+  int last = p0, ae = 0, la = l0, lb = l1, lc = l2;
+  if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; }
+  if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; }
+  const int row = (ae * 2) * B + la;
+  const R Iin = face_value<R>(fin, fstride, B, ae, lb, lc, T.ck[row], T.ck[row + B], T.cw[row], T.cw[row + B]);
+  const int idx0 = (int)((tb - reinterpret_cast<const unsigned char *>(tile)) / (long long)sizeof(vec2_t<R>));
+  return march<R>(tile, idx0, last, T.cev, Iin);
+}
+
 template <int MODE, int BC>
 __global__ void __launch_bounds__(kPairThreads, 3)
     cell_pair_kernel(GridDims g, int parts, int dt, const float *__restrict__ kappa, const float *__restrict__ S,
@@ -699,25 +714,33 @@ __global__ void __launch_bounds__(kPairThreads, 3)
       const int m0 = H2->sgn[0] > 0 ? mx : B - 1 - mx;
       const int m1 = H2->sgn[1] > 0 ? my : B - 1 - my;
       const int m2 = H2->sgn[2] > 0 ? mz : B - 1 - mz;
-      const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
-      int last = p0, ae = 0, la = l0, lb = l1, lc = l2, nb_ = m1, nc_ = m2;
-      if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; nb_ = m0; }
-      if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; nb_ = m0; nc_ = m1; }
-      const int row = (ae * 2) * B + la;
-      const int kb = T.ck[row], kc = T.ck[row + B];
-      const float2 wb = T.cw[row], wc = T.cw[row + B];
-      const float Iin1 = face_value<float>(fin1, fstride, B, ae, lb, lc, kb, kc, wb, wc);
-      const float Iin2 = face_value<float>(fin2, fstride, B, ae, nb_, nc_, kb, kc, wb, wc);
-      uint64_t I = pk2(Iin1, Iin2);
-      int e = last;
-      for (; e > 0; e -= 2) {
-        const TplEvent<float> e0 = T.cev[e], e1 = T.cev[e - 1];
-        segment_pair(t1, t2, e0, I);
-        segment_pair(t1, t2, e1, I);
-      }
-      if (e == 0) segment_pair(t1, t2, T.cev[0], I);
       float I1, I2;
-      upk2(I, I1, I2);
+      if (T.h->mirror) {
+        const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
+        int last = p0, ae = 0, la = l0, lb = l1, lc = l2, nb_ = m1, nc_ = m2;
+        if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; nb_ = m0; }
+        if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; nb_ = m0; nc_ = m1; }
+        const int row = (ae * 2) * B + la;
+        const int kb = T.ck[row], kc = T.ck[row + B];
+        const float2 wb = T.cw[row], wc = T.cw[row + B];
+        const float Iin1 = face_value<float>(fin1, fstride, B, ae, lb, lc, kb, kc, wb, wc);
+        const float Iin2 = face_value<float>(fin2, fstride, B, ae, nb_, nc_, kb, kc, wb, wc);
+        uint64_t I = pk2(Iin1, Iin2);
+        int e = last;
+        for (; e > 0; e -= 2) {
+          const TplEvent<float> e0 = T.cev[e], e1 = T.cev[e - 1];
+          segment_pair(t1, t2, e0, I);
+          segment_pair(t1, t2, e1, I);
+        }
+        if (e == 0) segment_pair(t1, t2, T.cev[0], I);
+        upk2(I, I1, I2);
+      } else {
+        // the pair's templates differ (near-tied plane crossings ordered
+        // differently): each ray follows its own direction's template
+        const Tpl<float> T2(buf + sb * j2, TL);
+        I1 = cell_ray<float>(T, fin1, fstride, B, l0, l1, l2, tile, t1);
+        I2 = cell_ray<float>(T2, fin2, fstride, B, m0, m1, m2, tile, t2);
+      }
       if (MODE == 1) {
         I_out[(long long)T.h->ext * g.ncell + gc1] = I1;
         I_out[(long long)H2->ext * g.ncell + gc2] = I2;

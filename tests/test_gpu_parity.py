@@ -98,10 +98,21 @@ def test_fp64_trace_and_closure_match_oracle(ora, case):
 
 
 # --------------------------------------------------------------- FP32 path
-@pytest.mark.parametrize("case", ["blob32", "lognormal48", "cloud", "ragged", "tiny_blocks"])
+@pytest.mark.parametrize("case", ["blob32", "lognormal48", "cloud", "ragged", "tiny_blocks", "unrotated8",
+                                  "unrotated16"])
 def test_fp32_closure_matches_oracle(ora, case):
+    """The unrotated cases hold directions with an exactly zero component (the
+    HEALPix equator ring, n_z = 0), where a direction and its antipode both
+    count the zero axis as positive: the paired cell pass must then take the
+    in-plane face coordinates of each ray from its own direction."""
     Ib = None
-    if case == "blob32":
+    if case == "unrotated8":
+        p = synth.blob_problem(n=16, B=8, nside=2, seed=1, rotate=False)
+        Ib = np.random.default_rng(24).uniform(0, 0.5, (6, 48))
+    elif case == "unrotated16":
+        p = synth.lognormal_problem(n=32, B=16, nside=4, seed=25, rotate=False)
+        Ib = np.random.default_rng(25).uniform(0, 0.5, (6, 192))
+    elif case == "blob32":
         p = synth.blob_problem(n=32, B=8, nside=2, seed=1)
     elif case == "lognormal48":
         p = synth.lognormal_problem(n=48, B=16, nside=4, seed=2)
