@@ -862,27 +862,63 @@ __global__ void floor_fix_blocks_kernel(const GridDims g, const int *__restrict_
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) moments_kernel(long long ncell, int ndir, const R *__restrict__ I,
+// Quadratures of stored intensities (Eqs. 10-12, c = 1): M[m][c] =
+// sum_k coef[k][m] I[k][c].  HBM-bound (4 bytes of I per 10 FMAs): one thread
+// per V consecutive cells with V-wide loads, directions unrolled by 4 so that
+// several loads are in flight, coefficients of a chunk of 64 directions in
+// shared memory.  The FP32 version keeps pairs of cells in packed f32x2
+// accumulators against (c, c) coefficient pairs.
+template <typename R, int V>
+__global__ void __launch_bounds__(256, 4) moments_kernel(long long ncell, int ndir, const R *__restrict__ I,
                                                       const R *__restrict__ coef, R *__restrict__ M) {
   __shared__ R cs[64][10];
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  R acc[10];
-  for (int m = 0; m < 10; ++m) acc[m] = R(0);
+  const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * V;
+  R acc[V][10];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < 10; ++m) acc[v][m] = R(0);
   for (int k0 = 0; k0 < ndir; k0 += 64) {
     const int nk = min(64, ndir - k0);
     __syncthreads();
     for (int i = threadIdx.x; i < nk * 10; i += blockDim.x) cs[i / 10][i % 10] = coef[(long long)k0 * 10 + i];
     __syncthreads();
     if (c < ncell) {
+#pragma unroll 4
       for (int k = 0; k < nk; ++k) {
-        const R v = I[(long long)(k0 + k) * ncell + c];
-        for (int m = 0; m < 10; ++m) acc[m] = fma(v, cs[k][m], acc[m]);
+        R v[V];
+        const R *src = I + (long long)(k0 + k) * ncell + c;
+        if (V == 4) {
+          const float4 q = *reinterpret_cast<const float4 *>(src);
+          v[0] = q.x; v[1] = q.y; v[V > 2 ? 2 : 0] = q.z; v[V > 3 ? 3 : 0] = q.w;
+        } else if (V == 2) {
+          const double2 q = *reinterpret_cast<const double2 *>(src);
+          v[0] = q.x; v[V > 1 ? 1 : 0] = q.y;
+        } else {
+          v[0] = src[0];
+        }
+#pragma unroll
+        for (int m = 0; m < 10; ++m) {
+          const R cm = cs[k][m];
+#pragma unroll
+          for (int j = 0; j < V; ++j) acc[j][m] = fma(v[j], cm, acc[j][m]);
+        }
       }
     }
   }
-  if (c < ncell)
-    for (int m = 0; m < 10; ++m) M[m * ncell + c] = acc[m];
+  if (c >= ncell) return;
+#pragma unroll
+  for (int m = 0; m < 10; ++m) {
+    R *dst = M + m * ncell + c;
+    if (V == 4) {
+      *reinterpret_cast<float4 *>(dst) = make_float4(acc[0][m], acc[V > 1 ? 1 : 0][m], acc[V > 2 ? 2 : 0][m],
+                                                     acc[V > 3 ? 3 : 0][m]);
+    } else if (V == 2) {
+      *reinterpret_cast<double2 *>(dst) = make_double2(acc[0][m], acc[V > 1 ? 1 : 0][m]);
+    } else {
+      dst[0] = acc[0][m];
+    }
+  }
 }
 
 int cell_parts(int B) {
@@ -1037,9 +1073,17 @@ cudaError_t launch_floor_fix_blocks(const GridDims &g, const int *block_list, in
 template <typename R>
 cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef, R *M_out, cudaStream_t st) {
   const int threads = 256;
-  const long long blocks = (ncell + threads - 1) / threads;
+  // vector loads need every direction's row to start 16-byte aligned
+  constexpr int VW = 16 / (int)sizeof(R);
+  const bool vec = ncell % VW == 0 && (reinterpret_cast<uintptr_t>(I) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(M_out) & 15) == 0;
+  const long long per = vec ? VW : 1;
+  const long long blocks = ((ncell + per - 1) / per + threads - 1) / threads;
   if (blocks < 1) return cudaSuccess;
-  moments_kernel<R><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out);
+  if (vec)
+    moments_kernel<R, VW><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out);
+  else
+    moments_kernel<R, 1><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out);
   return cudaGetLastError();
 }
 
