@@ -287,11 +287,12 @@ inline bool mirror_templates(const unsigned char *ta, const unsigned char *tb, i
 }
 
 // Face-pass schedule: level L of block b in octant o is b's upwind-ordered
-// index sum; one item = (block, up to `group` directions of one octant).
+// index sum; one item = (block, up to `group` directions of one octant), or
+// up to level_group[L] directions on level L when that table is given.
 // Writes level_off[0..nlevels] and, when items != nullptr, the items.
 // Returns the number of items, or -1 if it exceeds `cap`.
 inline long long build_schedule(const int nb[3], const int ob[9], int group, FaceItem *items, long long cap,
-                                int *level_off) {
+                                int *level_off, const int *level_group = nullptr) {
   const int nlevels = nb[0] + nb[1] + nb[2] - 2;
   // visit(L, f) calls f(block, d0, count) for every item of level L
   auto visit = [&](int L, auto &&f) {
@@ -311,7 +312,8 @@ inline long long build_schedule(const int nb[3], const int ob[9], int group, Fac
             // produces nothing any block reads
             if (lv != L || live == 0) continue;
             const int id = (bz * nb[1] + by) * nb[0] + bx;
-            for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += group) f(id, d0, std::min(group, ob[o + 1] - d0));
+            const int g = level_group ? level_group[L] : group;
+            for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += g) f(id, d0, std::min(g, ob[o + 1] - d0));
           }
     }
   };

@@ -30,6 +30,7 @@ struct vet_ctx {
   bool fp64 = false;
   std::vector<double> dirs_ext;  // [N][4] in HEALPix order
   std::vector<int> level_off;    // face items of level L: [level_off[L], level_off[L+1])
+  std::vector<int> level_group;  // directions per face item on level L
   void *d_tpl = nullptr;         // N template blobs, internal (octant-sorted) order
   FaceItem *d_items = nullptr;
   int *d_cell_order = nullptr;   // cell-pass visiting order of internal directions
@@ -99,14 +100,29 @@ void free_ctx(vet_ctx *c) {
 }
 
 // Face-pass schedule for `group` directions per item (uploaded; replaces the
-// previous one).
+// previous one).  A level whose items would not fill the GPU's face-pass
+// CTA slots once (two per SM) gets smaller items (group halved, down to one
+// direction): the first and last wavefront levels hold few blocks, and
+// shorter CTAs end them sooner.
 vet_status build_schedule(vet_ctx *c, int group) {
   const int nb[3] = {c->dims.nbx, c->dims.nby, c->dims.nbz};
   c->nlevels = nb[0] + nb[1] + nb[2] - 2;
-  std::vector<int> off(c->nlevels + 1, 0);
-  const long long nitems = vet::geom::build_schedule(nb, c->ob, group, nullptr, 1LL << 40, off.data());
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->cfg.device) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  const long long slots = 2LL * sms;
+  std::vector<int> lg(c->nlevels, group), off(c->nlevels + 1, 0);
+  for (int g = group / 2; g >= 1; g /= 2) {  // items per level at g directions per item
+    std::vector<int> prev(c->nlevels + 1, 0);
+    vet::geom::build_schedule(nb, c->ob, g * 2, nullptr, 1LL << 40, prev.data());
+    for (int L = 0; L < c->nlevels; ++L)
+      if (lg[L] == g * 2 && prev[L + 1] - prev[L] < slots) lg[L] = g;  // 2g left the level under one wave
+  }
+  const long long nitems = vet::geom::build_schedule(nb, c->ob, group, nullptr, 1LL << 40, off.data(), lg.data());
   std::vector<FaceItem> items((size_t)std::max<long long>(1, nitems));
-  vet::geom::build_schedule(nb, c->ob, group, items.data(), nitems, off.data());
+  vet::geom::build_schedule(nb, c->ob, group, items.data(), nitems, off.data(), lg.data());
   FaceItem *d = nullptr;
   cudaError_t e = cudaMalloc((void **)&d, sizeof(FaceItem) * items.size());
   if (e) return cuda_err(c, e, "cudaMalloc(schedule)");
@@ -117,6 +133,7 @@ vet_status build_schedule(vet_ctx *c, int group) {
   cudaFree(c->d_items);
   c->d_items = d;
   c->level_off = off;
+  c->level_group = lg;
   c->face_group = group;
   return VET_OK;
 }
@@ -328,7 +345,7 @@ vet_status run_face_pass(vet_ctx *c, const R *kappa, const R *S, const R *Ib, cu
   for (int L = 0; L < c->nlevels; ++L) {
     const int n = c->level_off[L + 1] - c->level_off[L];
     e = vet::launch_face_level<R>(c->dims, kappa, S, (const unsigned char *)c->d_tpl, c->d_items + c->level_off[L], n,
-                                  c->face_group, (R *)c->d_faces, (const R *)c->d_bnd, c->spin, c->d_status, st);
+                                  c->level_group[L], (R *)c->d_faces, (const R *)c->d_bnd, c->spin, c->d_status, st);
     if (e) return cuda_err(c, e, "face pass launch");
   }
   return VET_OK;

@@ -87,6 +87,26 @@ __device__ __forceinline__ R march(const vec2_t<R> *__restrict__ tile, int idx0,
   return I;
 }
 
+// march() with the event index shared by the lanes of a warp: from wl (the
+// warp's largest `last`) down to 0, a lane with e > last crosses an identity
+// segment (length 0, offset 0: the thin form returns I exactly).  Every event
+// index read is below the template's event capacity (3B).
+template <typename R>
+__device__ __forceinline__ R march_aligned(const vec2_t<R> *__restrict__ tile, int idx0, int last, int wl,
+                                           const TplEvent<R> *__restrict__ ev, R I) {
+  const unsigned char *tb = reinterpret_cast<const unsigned char *>(tile + idx0);
+  int e = wl;
+  for (; e > 0; e -= 2) {  // two segments per trip
+    TplEvent<R> e0 = ev[e], e1 = ev[e - 1];
+    if (e > last) { e0.len = R(0); e0.off = 0; }
+    if (e - 1 > last) { e1.len = R(0); e1.off = 0; }
+    segment<R>(tb, e0, I);
+    segment<R>(tb, e1, I);
+  }
+  if (e == 0 && last >= 0) segment<R>(tb, ev[0], I);
+  return I;
+}
+
 // Typed view of one direction's template blob.
 template <typename R>
 struct Tpl {
@@ -332,8 +352,12 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
       if (nb >= 0 && nb < nbb[a]) live |= a << (2 * nlive++);
     }
   }
-  const int NNL = nlive * NN;
-  for (int w = threadIdx.x; w < it.dir_count * NNL; w += blockDim.x) {
+  const int NNL = nlive * NN, total = it.dir_count * NNL;
+  // warp-uniform trips: lanes past the end redo the last node and store nothing
+  for (int w0 = (int)threadIdx.x & ~31; w0 < total; w0 += blockDim.x) {
+    const int wr = w0 + ((int)threadIdx.x & 31);
+    const bool act = wr < total;
+    const int w = act ? wr : total - 1;
     const int j = w / NNL, n = w - j * NNL;
     const Tpl<R> T(slots + sb * j, TL);
     const R *fin = reinterpret_cast<const R *>(slots + sb * j + TL.bytes);
@@ -350,13 +374,24 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     if (p2 < last) { last = p2; ae = 2; la = L2; lb = L0; lc = L1; }
     const int row = (ae * 2) * N1 + la;
     R I = face_value<R>(fin, g.fstride, B, ae, lb, lc, T.nk[row], T.nk[row + N1], T.nw[row], T.nw[row + N1]);
-    if (last >= 0) {  // then every L >= 1 and the start cell is inside the block
+    if (!act) last = -1;
+    // The lanes march in lockstep aligned at the downwind end: the warp runs
+    // from its largest `last` down to event 0, and a lane whose own ray is
+    // shorter crosses zero-length segments at its start cell (offset 0,
+    // length 0: the update returns I unchanged) until the event index
+    // reaches its `last`.  Lanes on one template then cross the same event
+    // at the same step, so their tile addresses are one common offset from
+    // neighbouring start cells (few shared-memory bank conflicts).
+    const int wl = __reduce_max_sync(0xffffffffu, last);
+    if (wl >= 0) {
+      // where last >= 0, every L >= 1 and the start cell is inside the block
       const int c0 = T.h->sgn[0] > 0 ? L0 - 1 : B - L0;
       const int c1 = T.h->sgn[1] > 0 ? L1 - 1 : B - L1;
       const int c2 = T.h->sgn[2] > 0 ? L2 - 1 : B - L2;
-      I = march<R>(tile, c0 + ts.sy * c1 + ts.sz * c2, last, T.nev, I);
+      const int idx0 = last >= 0 ? c0 + ts.sy * c1 + ts.sz * c2 : 0;
+      I = march_aligned<R>(tile, idx0, last, wl, T.nev, I);
     }
-    faces[(((long long)(it.dir_begin + j) * nblk + it.block) * 3 + a) * g.fstride + ub * W + uc] = I;
+    if (act) faces[(((long long)(it.dir_begin + j) * nblk + it.block) * 3 + a) * g.fstride + ub * W + uc] = I;
   }
 }
 
@@ -556,7 +591,9 @@ __global__ void __launch_bounds__(kCellThreads, 2)
 // in-plane face coordinates (which may differ along an axis the direction
 // does not cross) and the staged faces are per ray.  The cell order lists
 // the pairs (d, -d) consecutively; a staged tile holds dt / 2 pairs.
-constexpr int kPairThreads = 256;  // one lower-half cell and its mirror per thread
+// one lower-half cell and its mirror per thread; 512 threads (two CTAs per SM)
+// for 16^3 blocks, where three 256-thread CTAs would hold fewer warps
+__host__ __device__ constexpr int pair_threads(int B) { return B == 16 ? 512 : 256; }
 
 __device__ __forceinline__ uint64_t pk2(float a, float b) {
   return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
@@ -586,11 +623,10 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
 // and the same two forms as segment().
 __device__ __forceinline__ void segment_pair(const unsigned char *__restrict__ t1, const unsigned char *__restrict__ t2,
                                              const TplEvent<float> &ev, uint64_t &I) {
-  const float k1 = *reinterpret_cast<const float *>(t1 + ev.off);
-  const float s1 = *reinterpret_cast<const float *>(t1 + ev.off + 4);
-  const float k2 = *reinterpret_cast<const float *>(t2 - ev.off);
-  const float s2 = *reinterpret_cast<const float *>(t2 - ev.off + 4);
-  const uint64_t Y = mul2(pk2(k1, k2), pk2(ev.len, ev.len));
+  const float2 ks1 = *reinterpret_cast<const float2 *>(t1 + ev.off);  // (kappa, S): one 8-byte load
+  const float2 ks2 = *reinterpret_cast<const float2 *>(t2 - ev.off);
+  const float s1 = ks1.y, s2 = ks2.y;
+  const uint64_t Y = mul2(pk2(ks1.x, ks2.x), pk2(ev.len, ev.len));
   float y1, y2;
   upk2(Y, y1, y2);
   float e1, e2;
@@ -625,7 +661,7 @@ __device__ __forceinline__ R cell_ray(const Tpl<R> &T, const R *fin, int fstride
 }
 
 template <int MODE, int BC>
-__global__ void __launch_bounds__(kPairThreads, 3)
+__global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     cell_pair_kernel(GridDims g, int parts, int dt, const float *__restrict__ kappa, const float *__restrict__ S,
                      const unsigned char *__restrict__ tpl_g, const int *__restrict__ order,
                      const float *__restrict__ faces, const float *__restrict__ bnd, float *__restrict__ I_out,
@@ -667,7 +703,7 @@ __global__ void __launch_bounds__(kPairThreads, 3)
   __syncthreads();
 
   // this thread's lower-half cell (z < B/2): 4 x 4 x 2 bricks, warp-major
-  const int q = part * kPairThreads + (int)threadIdx.x;
+  const int q = part * pair_threads(BC) + (int)threadIdx.x;
   const int qb = q >> 5, ln = q & 31;
   const int cx = 4 * (qb % (B / 4)) + (ln & 3);
   const int cy = 4 * ((qb / (B / 4)) % (B / 4)) + ((ln >> 2) & 3);
@@ -953,10 +989,10 @@ template <int MODE, int BC>
 void pair_launch(const GridDims &g, const float *kappa, const float *S, const unsigned char *tpl, const int *order,
                  const float *faces, const float *bnd, float *I_out, float *M_out, float *E_out, float *f_out,
                  void *emax_bits, long long spin, int *status, const int *block_list, int nlist, cudaStream_t st) {
-  const int parts = BC * BC * BC / 2 / kPairThreads;
+  const int parts = BC * BC * BC / 2 / pair_threads(BC);
   const int nblk = block_list ? nlist : g.nbx * g.nby * g.nbz;
   const int dt = pair_dir_tile(BC, g.dir_tile);
-  cell_pair_kernel<MODE, BC><<<nblk * parts, kPairThreads, smem_bytes<float>(BC, 2 * dt), st>>>(
+  cell_pair_kernel<MODE, BC><<<nblk * parts, pair_threads(BC), smem_bytes<float>(BC, 2 * dt), st>>>(
       g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, status,
       block_list);
 }
