@@ -101,7 +101,7 @@ void free_ctx(vet_ctx *c) {
 
 // Face-pass schedule for `group` directions per item (uploaded; replaces the
 // previous one).  A level whose items would not fill the GPU's face-pass
-// CTA slots once (two per SM) gets smaller items (group halved, down to one
+// CTA slots once (three per SM) gets smaller items (group halved, down to one
 // direction): the first and last wavefront levels hold few blocks, and
 // shorter CTAs end them sooner.
 vet_status build_schedule(vet_ctx *c, int group) {
@@ -112,7 +112,7 @@ vet_status build_schedule(vet_ctx *c, int group) {
     cudaGetLastError();
     sms = 1;
   }
-  const long long slots = 2LL * sms;
+  const long long slots = 3LL * sms;
   std::vector<int> lg(c->nlevels, group), off(c->nlevels + 1, 0);
   for (int g = group / 2; g >= 1; g /= 2) {  // items per level at g directions per item
     std::vector<int> prev(c->nlevels + 1, 0);

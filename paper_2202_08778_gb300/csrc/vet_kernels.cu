@@ -308,7 +308,7 @@ inline int pair_dir_tile(int B, int want) {
 }
 
 template <typename R, int BC>
-__global__ void __launch_bounds__(kFaceThreads, 2)
+__global__ void __launch_bounds__(kFaceThreads, 3)
     face_pass_kernel(GridDims g, const R *__restrict__ kappa, const R *__restrict__ S,
                      const unsigned char *__restrict__ tpl_g, const FaceItem *__restrict__ items,
                      R *__restrict__ faces, const R *__restrict__ bnd, long long spin_limit, int *status) {
