@@ -318,8 +318,12 @@ def run_ours(args, rank, world, local_rank):
     cell_segs, face_segs = ctx.work_counts()
     launches = ctx.launches_per_closure()
 
-    tuning = ctx.autotune(kappa, S)  # the library's own tile choice, before timing
-    cfg["tuning"] = {"face_group": tuning[0], "dir_tile": tuning[1]}
+    if args.tuning:  # fixed tiles (profiling: the autotuner's timings are not meaningful under ncu)
+        ctx.set_tuning(*args.tuning)
+        tuning = ctx.tuning()
+    else:
+        tuning = ctx.autotune(kappa, S)  # the library's own tile choice, before timing
+    cfg["tuning"] = {"face_group": tuning[0], "dir_tile": tuning[1], "autotuned": not args.tuning}
     for _ in range(args.warmup):
         ctx.closure(kappa, S, None, f)
     ctx.set_timing(True)
@@ -403,7 +407,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure measurement")
+    ap.add_argument("--tuning", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    metavar="FG,DT", help="fixed face-pass direction group and cell-pass direction tile "
+                    "instead of autotuning")
     args = ap.parse_args()
+    if args.tuning is not None and len(args.tuning) != 2:
+        ap.error("--tuning takes two integers: FG,DT")
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))

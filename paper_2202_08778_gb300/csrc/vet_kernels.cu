@@ -358,10 +358,14 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
     const int wr = w0 + ((int)threadIdx.x & 31);
     const bool act = wr < total;
     const int w = act ? wr : total - 1;
-    const int j = w / NNL, n = w - j * NNL;
+    // w = (j * nlive + ai) * NN + r; NN is a compile-time constant for a
+    // templated block edge, and q / nlive (q < 3 * kMaxTune, nlive <= 3) is
+    // a multiply-shift instead of a runtime division
+    const int q = w / NN, r = w - q * NN;
+    const int j = nlive == 1 ? q : (nlive == 2 ? q >> 1 : (q * 21846) >> 16);
+    const int ai = q - j * nlive;
     const Tpl<R> T(slots + sb * j, TL);
     const R *fin = reinterpret_cast<const R *>(slots + sb * j + TL.bytes);
-    const int ai = n / NN, r = n - ai * NN;
     const int a = (live >> (2 * ai)) & 3;
     const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
     // upwind-frame node coordinates (L0, L1, L2): B along the face's axis
