@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "vet_internal.h"
 
@@ -257,6 +258,59 @@ inline bool antipodal_order(int N, const double *dirs, const int *order, int *ou
   return ok;
 }
 
+// Mirrored octant order for the paired face pass: within octant 7 - o (the
+// antipodes of octant o, o with a non-negative x component), internal
+// direction ob[7 - o] + k becomes the antipode of ob[o] + k.  Requires every
+// direction component to be non-zero (so that a direction and its antipode
+// lie in opposite octants) and the set to be closed under negation; returns
+// false, leaving `order` unchanged, otherwise.
+inline bool mirror_octant_order(int N, const double *dirs, int *order, const int ob[9]) {
+  for (int i = 0; i < N; ++i)
+    for (int a = 0; a < 3; ++a)
+      if (dirs[4 * i + a] == 0.0) return false;
+  std::vector<int> out(order, order + N);
+  for (int o = 0; o < 8; o += 2) {
+    const int m = 7 - o;
+    if (ob[o + 1] - ob[o] != ob[m + 1] - ob[m]) return false;
+    for (int k = 0; k < ob[o + 1] - ob[o]; ++k) {
+      const double *a = dirs + 4 * order[ob[o] + k];
+      int mate = -1;
+      for (int j = ob[m]; j < ob[m + 1] && mate < 0; ++j) {
+        const double *b = dirs + 4 * order[j];
+        if (std::fabs(a[0] + b[0]) < 1e-12 && std::fabs(a[1] + b[1]) < 1e-12 && std::fabs(a[2] + b[2]) < 1e-12)
+          mate = order[j];
+      }
+      if (mate < 0) return false;
+      out[ob[m] + k] = mate;
+    }
+  }
+  std::copy(out.begin(), out.end(), order);
+  return true;
+}
+
+// Whether the node-ray parts of two templates (of antipodal directions) are
+// exact mirror images, in the sense of mirror_templates for the cell rays.
+template <typename R>
+inline bool mirror_node_templates(const unsigned char *ta, const unsigned char *tb, int B) {
+  const TplLayout L = tpl_layout<R>(B);
+  const TplEvent<R> *ea = reinterpret_cast<const TplEvent<R> *>(ta + L.nev);
+  const TplEvent<R> *eb = reinterpret_cast<const TplEvent<R> *>(tb + L.nev);
+  double scale = 0.0;
+  for (int e = 0; e < 3 * B; ++e) scale = std::max(scale, std::fabs((double)ea[e].len));
+  for (int e = 0; e < 3 * B; ++e) {
+    const double la = ea[e].len, lb = eb[e].len;
+    if (std::fabs(la) <= 1e-9 * scale && std::fabs(lb) <= 1e-9 * scale) continue;
+    if (ea[e].off != -eb[e].off) return false;
+    if (std::fabs(la - lb) > 1e-6 * std::fabs(la)) return false;
+  }
+  if (std::memcmp(ta + L.npos, tb + L.npos, 3 * (B + 1) * 2) != 0) return false;
+  if (std::memcmp(ta + L.nk, tb + L.nk, 6 * (B + 1) * 2) != 0) return false;
+  const R *wa = reinterpret_cast<const R *>(ta + L.nw), *wb = reinterpret_cast<const R *>(tb + L.nw);
+  for (int i = 0; i < 6 * (B + 1) * 2; ++i)
+    if (std::fabs((double)wa[i] - (double)wb[i]) > 1e-6) return false;
+  return true;
+}
+
 // Whether the cell-ray parts of two templates (of antipodal directions) are
 // exact mirror images: equal event lengths (relative 1e-6) with negated
 // offsets, zero-length tie segments aside, and identical exit-event and
@@ -289,15 +343,20 @@ inline bool mirror_templates(const unsigned char *ta, const unsigned char *tb, i
 // Face-pass schedule: level L of block b in octant o is b's upwind-ordered
 // index sum; one item = (block, up to `group` directions of one octant), or
 // up to level_group[L] directions on level L when that table is given.
+// paired: only the octants with a non-negative x component are listed; an
+// item then also stands for the point-mirrored block (nb - 1 - b per axis,
+// at the same level) with the antipodal directions from mirror_begin on
+// (the order of mirror_octant_order).
 // Writes level_off[0..nlevels] and, when items != nullptr, the items.
 // Returns the number of items, or -1 if it exceeds `cap`.
 inline long long build_schedule(const int nb[3], const int ob[9], int group, FaceItem *items, long long cap,
-                                int *level_off, const int *level_group = nullptr) {
+                                int *level_off, const int *level_group = nullptr, bool paired = false) {
   const int nlevels = nb[0] + nb[1] + nb[2] - 2;
   // visit(L, f) calls f(block, d0, count) for every item of level L
   auto visit = [&](int L, auto &&f) {
-    for (int o = 0; o < 8; ++o) {
+    for (int o = 0; o < 8; o += paired ? 2 : 1) {
       if (ob[o + 1] == ob[o]) continue;
+      const int mshift = ob[7 - o] - ob[o];  // paired: antipode of d is d + mshift
       const int s[3] = {(o & 1) ? -1 : 1, (o & 2) ? -1 : 1, (o & 4) ? -1 : 1};
       for (int bz = 0; bz < nb[2]; ++bz)
         for (int by = 0; by < nb[1]; ++by)
@@ -313,20 +372,21 @@ inline long long build_schedule(const int nb[3], const int ob[9], int group, Fac
             if (lv != L || live == 0) continue;
             const int id = (bz * nb[1] + by) * nb[0] + bx;
             const int g = level_group ? level_group[L] : group;
-            for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += g) f(id, d0, std::min(g, ob[o + 1] - d0));
+            for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += g) f(id, d0, std::min(g, ob[o + 1] - d0), d0 + mshift);
           }
     }
   };
   long long total = 0;
   for (int L = 0; L < nlevels; ++L) {
     level_off[L] = (int)total;
-    visit(L, [&](int, int, int) { ++total; });
+    visit(L, [&](int, int, int, int) { ++total; });
   }
   level_off[nlevels] = (int)total;
   if (total > cap) return -1;
   if (!items) return total;
   long long k = 0;
-  for (int L = 0; L < nlevels; ++L) visit(L, [&](int id, int d0, int cnt) { items[k++] = {id, d0, cnt, 0}; });
+  for (int L = 0; L < nlevels; ++L)
+    visit(L, [&](int id, int d0, int cnt, int m0) { items[k++] = {id, d0, cnt, paired ? m0 : 0}; });
   return k;
 }
 

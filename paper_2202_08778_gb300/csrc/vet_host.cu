@@ -101,9 +101,9 @@ void free_ctx(vet_ctx *c) {
 
 // Face-pass schedule for `group` directions per item (uploaded; replaces the
 // previous one).  A level whose items would not fill the GPU's face-pass
-// CTA slots once (three per SM) gets smaller items (group halved, down to one
-// direction): the first and last wavefront levels hold few blocks, and
-// shorter CTAs end them sooner.
+// CTA slots once (three per SM, two for the paired face pass) gets smaller
+// items (group halved, down to one direction): the first and last wavefront
+// levels hold few blocks, and shorter CTAs end them sooner.
 vet_status build_schedule(vet_ctx *c, int group) {
   const int nb[3] = {c->dims.nbx, c->dims.nby, c->dims.nbz};
   c->nlevels = nb[0] + nb[1] + nb[2] - 2;
@@ -112,17 +112,19 @@ vet_status build_schedule(vet_ctx *c, int group) {
     cudaGetLastError();
     sms = 1;
   }
-  const long long slots = 3LL * sms;
+  const bool paired = c->dims.face_paired != 0;
+  const long long slots = (paired ? 2LL : 3LL) * sms;
   std::vector<int> lg(c->nlevels, group), off(c->nlevels + 1, 0);
   for (int g = group / 2; g >= 1; g /= 2) {  // items per level at g directions per item
     std::vector<int> prev(c->nlevels + 1, 0);
-    vet::geom::build_schedule(nb, c->ob, g * 2, nullptr, 1LL << 40, prev.data());
+    vet::geom::build_schedule(nb, c->ob, g * 2, nullptr, 1LL << 40, prev.data(), nullptr, paired);
     for (int L = 0; L < c->nlevels; ++L)
       if (lg[L] == g * 2 && prev[L + 1] - prev[L] < slots) lg[L] = g;  // 2g left the level under one wave
   }
-  const long long nitems = vet::geom::build_schedule(nb, c->ob, group, nullptr, 1LL << 40, off.data(), lg.data());
+  const long long nitems =
+      vet::geom::build_schedule(nb, c->ob, group, nullptr, 1LL << 40, off.data(), lg.data(), paired);
   std::vector<FaceItem> items((size_t)std::max<long long>(1, nitems));
-  vet::geom::build_schedule(nb, c->ob, group, items.data(), nitems, off.data(), lg.data());
+  vet::geom::build_schedule(nb, c->ob, group, items.data(), nitems, off.data(), lg.data(), paired);
   FaceItem *d = nullptr;
   cudaError_t e = cudaMalloc((void **)&d, sizeof(FaceItem) * items.size());
   if (e) return cuda_err(c, e, "cudaMalloc(schedule)");
@@ -144,6 +146,10 @@ vet_status build_context(vet_ctx *c) {
   std::vector<int> order(N);
   int ob[9];
   vet::geom::internal_order(N, c->dirs_ext.data(), order.data(), ob);
+  // FP32 face pass on mirrored block pairs: antipodes at equal positions of
+  // opposite octants (block edges 8 and 16, no zero direction component)
+  const bool mirror_order =
+      !c->fp64 && (B == 8 || B == 16) && vet::geom::mirror_octant_order(N, c->dirs_ext.data(), order.data(), ob);
   const int tbytes = vet::tpl_layout<R>(B).bytes;
   std::vector<unsigned char> tpl((size_t)tbytes * N);
   long long cs_tot = 0, ns_tot = 0;
@@ -175,6 +181,17 @@ vet_status build_context(vet_ctx *c) {
       reinterpret_cast<vet::TplHead<R> *>(ta)->mirror = m;
       reinterpret_cast<vet::TplHead<R> *>(tb)->mirror = m;
     }
+  }
+  // the face pass pairs (b, d) with (b', -d) only if every pair's node rays
+  // are exact mirror images (near-tied plane crossings can break this)
+  c->dims.face_paired = 0;
+  if (mirror_order) {
+    bool all = true;
+    for (int o = 0; o < 8 && all; o += 2)
+      for (int k = 0; k < ob[o + 1] - ob[o] && all; ++k)
+        all = vet::geom::mirror_node_templates<R>(tpl.data() + (size_t)(ob[o] + k) * tbytes,
+                                                  tpl.data() + (size_t)(ob[7 - o] + k) * tbytes, B);
+    c->dims.face_paired = all ? 1 : 0;
   }
   // moment coefficients in HEALPix order
   std::vector<R> coef((size_t)N * 10);

@@ -100,6 +100,7 @@ struct GridDims {
   long long ncell;    // nx*ny*nz
   int dir_tile;       // directions per cell-pass tile (0: default)
   int paired;         // 1: the cell order lists antipodal pairs (d, -d), see the paired cell pass
+  int face_paired;    // 1: face-pass items are mirrored block pairs, see the paired face pass
 };
 
 // Shared-memory kappa/S tiles of a block.  Face pass: cell (x, y, z) at
@@ -127,9 +128,9 @@ __host__ __device__ inline int face_stride_elems(int B) {
 // octant, all at the same wavefront level.
 struct FaceItem {
   int block;
-  int dir_begin;  // internal direction index
+  int dir_begin;     // internal direction index
   int dir_count;
-  int pad_;
+  int mirror_begin;  // paired face pass: internal index of the antipode of dir_begin
 };
 
 // Launchers (vet_kernels.cu).  All return the cudaGetLastError() of the

@@ -853,6 +853,162 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
   }
 }
 
+// ------------------------------------------- face pass, mirrored block pairs
+// FP32 face pass for block edges 8 and 16 and direction sets closed under
+// negation with no zero component.  The node ray of block b in direction d
+// from upwind-frame node coordinates L and the node ray of the point-mirrored
+// block b' (nb - 1 - b per axis) in direction -d from the same L are mirror
+// images: same exit event and exit-table entries, equal segment lengths, tile
+// offsets negated, and b' sits at the same wavefront level.  One CTA takes an
+// item (b, directions of one octant) together with (b', their antipodes); its
+// tile holds, per cell p of b, (kappa_b(p), kappa_b'(p'), S_b(p), S_b'(p'))
+// with p' the mirrored cell, so each step of a ray pair is one 16-byte load
+// already packed for the f32x2 arithmetic.  Only the staged incoming faces
+// differ between the two rays of a pair.
+
+// One segment of both rays on the paired tile (tb: the primary ray's start
+// entry; template offsets are for 8-byte entries, hence 2 * off).
+__device__ __forceinline__ void segment_pair_tile(const unsigned char *__restrict__ tb, const TplEvent<float> &ev,
+                                                  uint64_t &I) {
+  const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(tb + 2 * ev.off);  // (k, k'), (S, S')
+  const uint64_t Y = mul2(q.x, pk2(ev.len, ev.len));
+  float y1, y2;
+  upk2(Y, y1, y2);
+  float e1, e2;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(y1));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(y2));
+  uint64_t p = pk2(1.0833843353054956e-03f, 1.0833843353054956e-03f);
+  p = fma2(p, Y, pk2(9.4645342235962007e-03f, 9.4645342235962007e-03f));
+  p = fma2(p, Y, pk2(5.5464640186780434e-02f, 5.5464640186780434e-02f));
+  p = fma2(p, Y, pk2(2.4022290282685121e-01f, 2.4022290282685121e-01f));
+  p = fma2(p, Y, pk2(6.9314712699664371e-01f, 6.9314712699664371e-01f));
+  float n1, n2;  // -(1 - e^-x) of the thin form
+  upk2(mul2(p, Y), n1, n2);
+  const bool thin1 = y1 > -0.7213475204444817f, thin2 = y2 > -0.7213475204444817f;
+  float i1, i2, s1, s2;
+  upk2(I, i1, i2);
+  upk2(q.y, s1, s2);
+  I = fma2(sub2(I, q.y), pk2(thin1 ? n1 : e1, thin2 ? n2 : e2), pk2(thin1 ? i1 : s1, thin2 ? i2 : s2));
+}
+
+template <int BC>
+__device__ __forceinline__ void load_tile_mirrored(float4 *tile, TileShape ts, const GridDims &g, int bx, int by,
+                                                   int bz, int mx, int my, int mz, const float *__restrict__ kappa,
+                                                   const float *__restrict__ S) {
+  constexpr int B = BC, B2 = B * B, B3 = B2 * B;
+  for (int i = threadIdx.x; i < B3; i += blockDim.x) {
+    const int x = i % B, y = (i / B) % B, z = i / B2;
+    const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
+    const long long gm =
+        ((long long)(mz * B + B - 1 - z) * g.ny + (my * B + B - 1 - y)) * g.nx + (mx * B + B - 1 - x);
+    tile[x + ts.sy * y + ts.sz * z] = make_float4(kappa[gi], kappa[gm], S[gi], S[gm]);
+  }
+}
+
+__host__ __device__ inline size_t face_pair_smem_bytes(int B, int nslots) {
+  return align16(sizeof(float4) * (size_t)node_tile(B).elems) + (size_t)nslots * slot_bytes<float>(B);
+}
+
+template <int BC>
+__global__ void __launch_bounds__(kFaceThreads, 2)
+    face_pair_kernel(GridDims g, const float *__restrict__ kappa, const float *__restrict__ S,
+                     const unsigned char *__restrict__ tpl_g, const FaceItem *__restrict__ items,
+                     float *__restrict__ faces, const float *__restrict__ bnd, long long spin_limit, int *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full;
+  constexpr int B = BC, W = B + 2, N1 = B + 1, NN = N1 * N1;
+  const TileShape ts = node_tile(B);
+  const TplLayout TL = tpl_layout<float>(B);
+  const size_t sb = slot_bytes<float>(B);
+  const FaceItem it = items[blockIdx.x];
+  float4 *tile = reinterpret_cast<float4 *>(smem);
+  // slots: the item's directions for b, then their antipodes for b'
+  unsigned char *slots = smem + align16(sizeof(float4) * (size_t)ts.elems);
+  const int bx = it.block % g.nbx, by = (it.block / g.nbx) % g.nby, bz = it.block / (g.nbx * g.nby);
+  const int mx = g.nbx - 1 - bx, my = g.nby - 1 - by, mz = g.nbz - 1 - bz;
+  const int mblock = (mz * g.nby + my) * g.nbx + mx;
+  const int nblk = g.nbx * g.nby * g.nbz;
+  const int cnt = it.dir_count;
+  if (threadIdx.x == 0) {
+    mbar_init(&full, 1);
+    mbar_fence_init();
+    mbar_expect_tx(&full, (uint32_t)(sb * 2 * cnt));
+    for (int j = 0; j < cnt; ++j) {
+      issue_slot<float>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full);
+      issue_slot<float>(slots + sb * (cnt + j), g, TL, mx, my, mz, it.mirror_begin + j, tpl_g, faces, bnd, &full);
+    }
+  }
+  load_tile_mirrored<BC>(tile, ts, g, bx, by, bz, mx, my, mz, kappa, S);
+  __syncthreads();
+  if (!mbar_wait_warp(&full, 0, spin_limit, status, 1)) {
+    if (threadIdx.x == 0) mbar_wait(&full, 0, kDrainPolls, status, 8);
+    return;
+  }
+  // live axes (downwind neighbour exists): the same for b in d and b' in -d
+  int live = 0, nlive = 0;
+  {
+    const TplHead<float> *h0 = reinterpret_cast<const TplHead<float> *>(slots);
+    const int bb[3] = {bx, by, bz}, nbb[3] = {g.nbx, g.nby, g.nbz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int nb = bb[a] + h0->sgn[a];
+      if (nb >= 0 && nb < nbb[a]) live |= a << (2 * nlive++);
+    }
+  }
+  const int total = cnt * nlive * NN;
+  for (int w0 = (int)threadIdx.x & ~31; w0 < total; w0 += blockDim.x) {
+    const int wr = w0 + ((int)threadIdx.x & 31);
+    const bool act = wr < total;
+    const int w = act ? wr : total - 1;
+    const int q = w / NN, r = w - q * NN;
+    const int j = nlive == 1 ? q : (nlive == 2 ? q >> 1 : (q * 21846) >> 16);
+    const int ai = q - j * nlive;
+    const Tpl<float> T(slots + sb * j, TL);
+    const float *fin1 = reinterpret_cast<const float *>(slots + sb * j + TL.bytes);
+    const float *fin2 = reinterpret_cast<const float *>(slots + sb * (cnt + j) + TL.bytes);
+    const int a = (live >> (2 * ai)) & 3;
+    const int ub = r / N1, uc = r - ub * N1;
+    const int L0 = a == 0 ? B : ub;
+    const int L1 = a == 1 ? B : (a == 0 ? ub : uc);
+    const int L2 = a == 2 ? B : uc;
+    const int p0 = T.npos[L0], p1 = T.npos[N1 + L1], p2 = T.npos[2 * N1 + L2];
+    int last = p0, ae = 0, la = L0, lb = L1, lc = L2;
+    if (p1 < last) { last = p1; ae = 1; la = L1; lb = L0; }
+    if (p2 < last) { last = p2; ae = 2; la = L2; lb = L0; lc = L1; }
+    const int row = (ae * 2) * N1 + la;
+    const int kb = T.nk[row], kc = T.nk[row + N1];
+    const float2 wb = T.nw[row], wc = T.nw[row + N1];
+    uint64_t I = pk2(face_value<float>(fin1, g.fstride, B, ae, lb, lc, kb, kc, wb, wc),
+                     face_value<float>(fin2, g.fstride, B, ae, lb, lc, kb, kc, wb, wc));
+    if (!act) last = -1;
+    // lockstep aligned at the downwind end, as in the unpaired face pass
+    const int wl = __reduce_max_sync(0xffffffffu, last);
+    if (wl >= 0) {
+      const int c0 = T.h->sgn[0] > 0 ? L0 - 1 : B - L0;
+      const int c1 = T.h->sgn[1] > 0 ? L1 - 1 : B - L1;
+      const int c2 = T.h->sgn[2] > 0 ? L2 - 1 : B - L2;
+      const int idx0 = last >= 0 ? c0 + ts.sy * c1 + ts.sz * c2 : 0;
+      const unsigned char *tb = reinterpret_cast<const unsigned char *>(tile + idx0);
+      int e = wl;
+      for (; e > 0; e -= 2) {
+        TplEvent<float> e0 = T.nev[e], e1 = T.nev[e - 1];
+        if (e > last) { e0.len = 0.f; e0.off = 0; }
+        if (e - 1 > last) { e1.len = 0.f; e1.off = 0; }
+        segment_pair_tile(tb, e0, I);
+        segment_pair_tile(tb, e1, I);
+      }
+      if (e == 0 && last >= 0) segment_pair_tile(tb, T.nev[0], I);
+    }
+    if (act) {
+      float I1, I2;
+      upk2(I, I1, I2);
+      const int node = ub * W + uc;
+      faces[(((long long)(it.dir_begin + j) * nblk + it.block) * 3 + a) * g.fstride + node] = I1;
+      faces[(((long long)(it.mirror_begin + j) * nblk + mblock) * 3 + a) * g.fstride + node] = I2;
+    }
+  }
+}
+
 // Boundary faces of every direction, materialised so that staging is a
 // plain bulk copy: bnd[face][d][i] = Ib[face][ext(d)] (0 for vacuum).
 template <typename R>
@@ -971,6 +1127,13 @@ int cell_parts(int B) {
 template <typename R, int BC>
 void face_launch(const GridDims &g, const R *kappa, const R *S, const unsigned char *tpl, const FaceItem *items,
                  int nitems, int max_dirs, R *faces, const R *bnd, long long spin, int *status, cudaStream_t st) {
+  if constexpr (sizeof(R) == sizeof(float) && BC != 0) {
+    if (g.face_paired) {
+      face_pair_kernel<BC><<<nitems, kFaceThreads, face_pair_smem_bytes(BC, 2 * max_dirs), st>>>(
+          g, kappa, S, tpl, items, faces, bnd, spin, status);
+      return;
+    }
+  }
   face_pass_kernel<R, BC><<<nitems, kFaceThreads, smem_bytes<R>(g.B, max_dirs), st>>>(g, kappa, S, tpl, items, faces,
                                                                                       bnd, spin, status);
 }
@@ -1016,7 +1179,8 @@ cudaError_t set_smem_attrs() {
   }
   const void *pfns[] = {(const void *)cell_pair_kernel<0, 8>,  (const void *)cell_pair_kernel<0, 16>,
                         (const void *)cell_pair_kernel<1, 8>,  (const void *)cell_pair_kernel<1, 16>,
-                        (const void *)cell_pair_kernel<2, 8>,  (const void *)cell_pair_kernel<2, 16>};
+                        (const void *)cell_pair_kernel<2, 8>,  (const void *)cell_pair_kernel<2, 16>,
+                        (const void *)face_pair_kernel<8>,     (const void *)face_pair_kernel<16>};
   for (const void *f : pfns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
