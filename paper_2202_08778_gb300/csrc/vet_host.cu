@@ -510,7 +510,8 @@ VET_API vet_status vet_create(vet_ctx **out, const vet_grid *grid, const vet_con
   if (!(qn > 1e-12) || !std::isfinite(qn)) return set_err(nullptr, VET_EINVAL, "rotation quaternion is zero or not finite");
   const bool fp64 = cfg->precision == VET_FP64;
   const int nnode = (g.block + 1) * (g.block + 1);
-  if (vet::pass_smem_bytes(g.block, vet::kFaceGroup, fp64) > 232448 - 64)
+  if (vet::pass_smem_bytes(g.block, vet::kFaceGroup, fp64) > 232448 - 64 ||
+      vet::cell_smem_bytes(g.block, 2, fp64) > 232448 - 64)
     return set_err(nullptr, VET_EUNSUPPORTED, "block edge too large for one CTA's shared memory at this precision");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {

@@ -59,16 +59,19 @@ struct alignas(2 * sizeof(R)) TplEvent {
   int off;
 };
 
+// The head and the node-ray parts come first, so that the face pass stages
+// only [0, node_bytes) of a template.
 struct TplLayout {
-  int cev;    // TplEvent<R>[3B]  cell-ray events
-  int nev;    // TplEvent<R>[3B]  node-ray events
-  int cpos;   // int16[3][B]  merged index of cell event (a, m)
-  int npos;   // int16[3][B+1] merged index of node event (a, m); [a][0] = -1
-  int ck;     // int16[3][2][B]   floor(d) of cell exits
-  int cw;     // R[3][2][B][2]    (f, 1-f) of cell exits
-  int nk;     // int16[3][2][B+1] floor(d) of node exits
-  int nw;     // R[3][2][B+1][2]  (f, 1-f) of node exits
-  int bytes;  // total, a multiple of 16
+  int nev;         // TplEvent<R>[3B]  node-ray events
+  int npos;        // int16[3][B+1] merged index of node event (a, m); [a][0] = -1
+  int nk;          // int16[3][2][B+1] floor(d) of node exits
+  int nw;          // R[3][2][B+1][2]  (f, 1-f) of node exits
+  int node_bytes;  // head and node-ray parts, a multiple of 16
+  int cev;         // TplEvent<R>[3B]  cell-ray events
+  int cpos;        // int16[3][B]  merged index of cell event (a, m)
+  int ck;          // int16[3][2][B]   floor(d) of cell exits
+  int cw;          // R[3][2][B][2]    (f, 1-f) of cell exits
+  int bytes;       // total, a multiple of 16
 };
 
 __host__ __device__ inline int tpl_align16(int x) { return (x + 15) & ~15; }
@@ -77,14 +80,15 @@ template <typename R>
 __host__ __device__ inline TplLayout tpl_layout(int B) {
   TplLayout L;
   int o = tpl_align16((int)sizeof(TplHead<R>));
-  L.cev = o;  o = tpl_align16(o + 3 * B * (int)sizeof(TplEvent<R>));
   L.nev = o;  o = tpl_align16(o + 3 * B * (int)sizeof(TplEvent<R>));
-  L.cpos = o; o = tpl_align16(o + 3 * B * 2);
   L.npos = o; o = tpl_align16(o + 3 * (B + 1) * 2);
-  L.ck = o;   o = tpl_align16(o + 6 * B * 2);
-  L.cw = o;   o = tpl_align16(o + 6 * B * 2 * (int)sizeof(R));
   L.nk = o;   o = tpl_align16(o + 6 * (B + 1) * 2);
   L.nw = o;   o = tpl_align16(o + 6 * (B + 1) * 2 * (int)sizeof(R));
+  L.node_bytes = o;
+  L.cev = o;  o = tpl_align16(o + 3 * B * (int)sizeof(TplEvent<R>));
+  L.cpos = o; o = tpl_align16(o + 3 * B * 2);
+  L.ck = o;   o = tpl_align16(o + 6 * B * 2);
+  L.cw = o;   o = tpl_align16(o + 6 * B * 2 * (int)sizeof(R));
   L.bytes = o;
   return L;
 }
@@ -174,14 +178,15 @@ template <typename R>
 cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef, R *M_out,
                            cudaStream_t st);
 
-// Dynamic shared memory of a CTA staging `dirs` directions.
+// Dynamic shared memory of an unpaired face-pass CTA staging `dirs` directions.
 size_t pass_smem_bytes(int B, int dirs, bool fp64);
 
 // Largest cell-pass direction tile (<= want) whose two buffers fit.
 int cell_tile_fit(int B, int want, bool fp64);
 
-// Bytes of one staged direction (template + three faces).
-size_t face_slot_bytes(int B, bool fp64);
+// Dynamic shared memory of an unpaired cell-pass CTA with `nslots` staged
+// directions.
+size_t cell_smem_bytes(int B, int nslots, bool fp64);
 
 // Directions per face-pass item (default; a context may be tuned to 1..8).
 constexpr int kFaceGroup = 4;

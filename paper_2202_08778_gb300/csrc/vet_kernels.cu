@@ -223,12 +223,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // copies of internal direction d for block (bx, by, bz); the faces come from
 // the upwind neighbours' stored downwind faces or from the materialised
 // boundary faces bnd[face][d].
+// tpl_bytes: the leading part of the template staged (TL.bytes for the cell
+// passes, TL.node_bytes for the face pass; 0 stages the faces alone); the
+// faces follow it in the slot.
 template <typename R>
 __device__ __forceinline__ void issue_slot(unsigned char *slot, const GridDims &g, const TplLayout &TL, int bx,
                                            int by, int bz, int d, const unsigned char *__restrict__ tpl_g,
-                                           const R *__restrict__ faces, const R *__restrict__ bnd, uint64_t *bar) {
+                                           const R *__restrict__ faces, const R *__restrict__ bnd, uint64_t *bar,
+                                           int tpl_bytes) {
   const unsigned char *src = tpl_g + (size_t)d * TL.bytes;
-  bulk_g2s(slot, src, (uint32_t)TL.bytes, bar);
+  if (tpl_bytes > 0) bulk_g2s(slot, src, (uint32_t)tpl_bytes, bar);
   const TplHead<R> *hd = reinterpret_cast<const TplHead<R> *>(src);
   const int nblk = g.nbx * g.nby * g.nbz;
   const uint32_t fb = (uint32_t)(g.fstride * sizeof(R));
@@ -246,13 +250,24 @@ __device__ __forceinline__ void issue_slot(unsigned char *slot, const GridDims &
       const long long nid = ((long long)nb[2] * g.nby + nb[1]) * g.nbx + nb[0];
       fsrc = faces + (((long long)d * nblk + nid) * 3 + a) * g.fstride;
     }
-    bulk_g2s(slot + TL.bytes + a * fb, fsrc, fb, bar);
+    bulk_g2s(slot + tpl_bytes + a * fb, fsrc, fb, bar);
   }
 }
 
+// Bytes of the three staged incoming faces of one direction.
+template <typename R>
+__host__ __device__ inline size_t faces_bytes(int B) {
+  return sizeof(R) * 3 * (size_t)face_stride_elems<R>(B);
+}
+// One staged direction of the cell passes (whole template and faces) and of
+// the face pass (head and node-ray parts, faces).
 template <typename R>
 __host__ __device__ inline size_t slot_bytes(int B) {
-  return (size_t)tpl_layout<R>(B).bytes + sizeof(R) * 3 * (size_t)face_stride_elems<R>(B);
+  return (size_t)tpl_layout<R>(B).bytes + faces_bytes<R>(B);
+}
+template <typename R>
+__host__ __device__ inline size_t face_slot_bytes_t(int B) {
+  return (size_t)tpl_layout<R>(B).node_bytes + faces_bytes<R>(B);
 }
 
 template <typename R, int BC>
@@ -272,11 +287,15 @@ __device__ __forceinline__ void load_tile(vec2_t<R> *tile, TileShape ts, const G
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Dynamic shared memory of a CTA holding `nslots` staged directions.
+// Dynamic shared memory of a cell-pass CTA holding `nslots` staged directions.
 template <typename R>
 __host__ __device__ inline size_t smem_bytes(int B, int nslots) {
-  const int te = node_tile(B).elems > cell_tile(B).elems ? node_tile(B).elems : cell_tile(B).elems;
-  return align16(sizeof(vec2_t<R>) * (size_t)te) + (size_t)nslots * slot_bytes<R>(B);
+  return align16(sizeof(vec2_t<R>) * (size_t)cell_tile(B).elems) + (size_t)nslots * slot_bytes<R>(B);
+}
+// ... and of an unpaired face-pass CTA.
+template <typename R>
+__host__ __device__ inline size_t face_smem_bytes(int B, int nslots) {
+  return align16(sizeof(vec2_t<R>) * (size_t)node_tile(B).elems) + (size_t)nslots * face_slot_bytes_t<R>(B);
 }
 
 constexpr int kDirTile = 4;   // directions per cell-pass tile (two tiles in flight)
@@ -318,7 +337,7 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
   const int W = B + 2, N1 = B + 1, NN = N1 * N1;
   const TileShape ts = node_tile(B);
   const TplLayout TL = tpl_layout<R>(B);
-  const size_t sb = slot_bytes<R>(B);
+  const size_t sb = face_slot_bytes_t<R>(B);
   const FaceItem it = items[blockIdx.x];
   vec2_t<R> *tile = reinterpret_cast<vec2_t<R> *>(smem);
   unsigned char *slots = smem + align16(sizeof(vec2_t<R>) * (size_t)ts.elems);
@@ -329,7 +348,7 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
     mbar_fence_init();
     mbar_expect_tx(&full, (uint32_t)(sb * it.dir_count));
     for (int j = 0; j < it.dir_count; ++j)
-      issue_slot<R>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full);
+      issue_slot<R>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full, TL.node_bytes);
   }
   load_tile<R, BC>(tile, ts, g, bx, by, bz, kappa, S);
   __syncthreads();
@@ -365,7 +384,7 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
     const int j = nlive == 1 ? q : (nlive == 2 ? q >> 1 : (q * 21846) >> 16);
     const int ai = q - j * nlive;
     const Tpl<R> T(slots + sb * j, TL);
-    const R *fin = reinterpret_cast<const R *>(slots + sb * j + TL.bytes);
+    const R *fin = reinterpret_cast<const R *>(slots + sb * j + TL.node_bytes);
     const int a = (live >> (2 * ai)) & 3;
     const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
     // upwind-frame node coordinates (L0, L1, L2): B along the face's axis
@@ -445,7 +464,8 @@ __global__ void __launch_bounds__(kCellThreads, 2)
     const int b = t & 1, d0 = t * dt, nd = min(dt, g.ndir - d0);
     unsigned char *buf = buf0 + (size_t)b * dt * sb;
     mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
-    for (int j = 0; j < nd; ++j) issue_slot<R>(buf + sb * j, g, TL, bx, by, bz, order[d0 + j], tpl_g, faces, bnd, &full[b]);
+    for (int j = 0; j < nd; ++j)
+      issue_slot<R>(buf + sb * j, g, TL, bx, by, bz, order[d0 + j], tpl_g, faces, bnd, &full[b], TL.bytes);
   };
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -692,7 +712,7 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     unsigned char *buf = buf0 + (size_t)b * dt * sb;
     mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
     for (int j = 0; j < nd; ++j)
-      issue_slot<float>(buf + sb * j, g, TL, bx, by, bz, order[d0 + j], tpl_g, faces, bnd, &full[b]);
+      issue_slot<float>(buf + sb * j, g, TL, bx, by, bz, order[d0 + j], tpl_g, faces, bnd, &full[b], TL.bytes);
   };
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -905,8 +925,10 @@ __device__ __forceinline__ void load_tile_mirrored(float4 *tile, TileShape ts, c
   }
 }
 
-__host__ __device__ inline size_t face_pair_smem_bytes(int B, int nslots) {
-  return align16(sizeof(float4) * (size_t)node_tile(B).elems) + (size_t)nslots * slot_bytes<float>(B);
+// Dynamic shared memory of a paired face-pass CTA for `dirs` direction pairs.
+__host__ __device__ inline size_t face_pair_smem_bytes(int B, int dirs) {
+  return align16(sizeof(float4) * (size_t)node_tile(B).elems) +
+         (size_t)dirs * (face_slot_bytes_t<float>(B) + faces_bytes<float>(B));
 }
 
 template <int BC>
@@ -919,10 +941,12 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
   constexpr int B = BC, W = B + 2, N1 = B + 1, NN = N1 * N1;
   const TileShape ts = node_tile(B);
   const TplLayout TL = tpl_layout<float>(B);
-  const size_t sb = slot_bytes<float>(B);
+  const size_t sb = face_slot_bytes_t<float>(B), fb3 = faces_bytes<float>(B);
   const FaceItem it = items[blockIdx.x];
   float4 *tile = reinterpret_cast<float4 *>(smem);
-  // slots: the item's directions for b, then their antipodes for b'
+  // slots: the item's directions for b (node template parts and faces), then
+  // the incoming faces of b' for their antipodes (whose node rays follow the
+  // primary templates)
   unsigned char *slots = smem + align16(sizeof(float4) * (size_t)ts.elems);
   const int bx = it.block % g.nbx, by = (it.block / g.nbx) % g.nby, bz = it.block / (g.nbx * g.nby);
   const int mx = g.nbx - 1 - bx, my = g.nby - 1 - by, mz = g.nbz - 1 - bz;
@@ -932,10 +956,12 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
   if (threadIdx.x == 0) {
     mbar_init(&full, 1);
     mbar_fence_init();
-    mbar_expect_tx(&full, (uint32_t)(sb * 2 * cnt));
+    mbar_expect_tx(&full, (uint32_t)((sb + fb3) * cnt));
     for (int j = 0; j < cnt; ++j) {
-      issue_slot<float>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full);
-      issue_slot<float>(slots + sb * (cnt + j), g, TL, mx, my, mz, it.mirror_begin + j, tpl_g, faces, bnd, &full);
+      issue_slot<float>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full,
+                        TL.node_bytes);
+      issue_slot<float>(slots + sb * cnt + fb3 * j, g, TL, mx, my, mz, it.mirror_begin + j, tpl_g, faces, bnd,
+                        &full, 0);
     }
   }
   load_tile_mirrored<BC>(tile, ts, g, bx, by, bz, mx, my, mz, kappa, S);
@@ -964,8 +990,8 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     const int j = nlive == 1 ? q : (nlive == 2 ? q >> 1 : (q * 21846) >> 16);
     const int ai = q - j * nlive;
     const Tpl<float> T(slots + sb * j, TL);
-    const float *fin1 = reinterpret_cast<const float *>(slots + sb * j + TL.bytes);
-    const float *fin2 = reinterpret_cast<const float *>(slots + sb * (cnt + j) + TL.bytes);
+    const float *fin1 = reinterpret_cast<const float *>(slots + sb * j + TL.node_bytes);
+    const float *fin2 = reinterpret_cast<const float *>(slots + sb * cnt + fb3 * j);
     const int a = (live >> (2 * ai)) & 3;
     const int ub = r / N1, uc = r - ub * N1;
     const int L0 = a == 0 ? B : ub;
@@ -1129,13 +1155,13 @@ void face_launch(const GridDims &g, const R *kappa, const R *S, const unsigned c
                  int nitems, int max_dirs, R *faces, const R *bnd, long long spin, int *status, cudaStream_t st) {
   if constexpr (sizeof(R) == sizeof(float) && BC != 0) {
     if (g.face_paired) {
-      face_pair_kernel<BC><<<nitems, kFaceThreads, face_pair_smem_bytes(BC, 2 * max_dirs), st>>>(
+      face_pair_kernel<BC><<<nitems, kFaceThreads, face_pair_smem_bytes(BC, max_dirs), st>>>(
           g, kappa, S, tpl, items, faces, bnd, spin, status);
       return;
     }
   }
-  face_pass_kernel<R, BC><<<nitems, kFaceThreads, smem_bytes<R>(g.B, max_dirs), st>>>(g, kappa, S, tpl, items, faces,
-                                                                                      bnd, spin, status);
+  face_pass_kernel<R, BC><<<nitems, kFaceThreads, face_smem_bytes<R>(g.B, max_dirs), st>>>(g, kappa, S, tpl, items,
+                                                                                           faces, bnd, spin, status);
 }
 
 template <typename R, int MODE, int BC>
@@ -1292,14 +1318,16 @@ cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef,
 }
 
 size_t pass_smem_bytes(int B, int dirs, bool fp64) {
-  return fp64 ? smem_bytes<double>(B, dirs) : smem_bytes<float>(B, dirs);
+  return fp64 ? face_smem_bytes<double>(B, dirs) : face_smem_bytes<float>(B, dirs);
 }
 
 int cell_tile_fit(int B, int want, bool fp64) {
   return fp64 ? cell_dir_tile<double>(B, want) : cell_dir_tile<float>(B, want);
 }
 
-size_t face_slot_bytes(int B, bool fp64) { return fp64 ? slot_bytes<double>(B) : slot_bytes<float>(B); }
+size_t cell_smem_bytes(int B, int nslots, bool fp64) {
+  return fp64 ? smem_bytes<double>(B, nslots) : smem_bytes<float>(B, nslots);
+}
 
 // Opt the shared-memory-heavy kernels in to the full 227 KB per CTA on the
 // current device (the attribute is per device and function).
