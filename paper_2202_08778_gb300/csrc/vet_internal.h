@@ -107,12 +107,15 @@ struct GridDims {
   int face_paired;    // 1: face-pass items are mirrored block pairs, see the paired face pass
 };
 
-// Shared-memory kappa/S tiles of a block.  Face pass: cell (x, y, z) at
-// x + (B+1) y + (B+1)^2 z; the three strides are odd, so a warp walking a row,
-// column or pillar of a face (and any uniform shift of it) touches distinct
-// banks with its 8-byte loads.  Cell pass: x + (B+4) y + (B+4) B z; with B a
-// multiple of 8 the y stride is 4 or 12 mod 16, so a 4 x 4 layer of a warp's
-// 4 x 4 x 2 cell brick is conflict free.
+// Shared-memory kappa/S tiles of a block, in entries of 8 bytes (kappa, S) or,
+// for the FP32 mirrored passes, 16 bytes (kappa, kappa', S, S').  Face pass:
+// cell (x, y, z) at x + (B+1) y + (B+1)^2 z; the three strides are odd, so a
+// warp walking a row, column or pillar of a face (and any uniform shift of
+// it) touches distinct banks.  Cell pass: x + (B+4) y + (B+4) B z; with B a
+// multiple of 8 the y stride is 4 or 12 mod 16 entries of 8 bytes (a 4 x 4
+// layer of a warp's 4 x 4 x 2 cell brick is conflict free) and 4 mod 8
+// entries of 16 bytes (each quarter warp, 4 x 2 cells, covers the 32 banks
+// once).
 struct TileShape {
   int sy, sz, elems;
 };

@@ -298,6 +298,11 @@ __host__ __device__ inline size_t face_smem_bytes(int B, int nslots) {
   return align16(sizeof(vec2_t<R>) * (size_t)node_tile(B).elems) + (size_t)nslots * face_slot_bytes_t<R>(B);
 }
 
+// ... and of a paired cell-pass CTA (16-byte tile entries).
+__host__ __device__ inline size_t pair_smem_bytes(int B, int nslots) {
+  return align16(sizeof(float4) * (size_t)cell_tile(B).elems) + (size_t)nslots * slot_bytes<float>(B);
+}
+
 constexpr int kDirTile = 4;   // directions per cell-pass tile (two tiles in flight)
 constexpr size_t kSmemMax = 232448 - 64;  // opt-in limit less the static mbarriers
 
@@ -322,7 +327,7 @@ inline int pair_dir_tile(int B, int want) {
   int dt = want > 0 ? want : kDirTile;
   dt = (dt + 1) & ~1;
   if (dt > kMaxTune) dt = kMaxTune;
-  while (dt > 2 && smem_bytes<float>(B, 2 * dt) > kSmemMax) dt -= 2;
+  while (dt > 2 && pair_smem_bytes(B, 2 * dt) > kSmemMax) dt -= 2;
   return dt;
 }
 
@@ -610,11 +615,14 @@ __global__ void __launch_bounds__(kCellThreads, 2)
 // start at the same coordinates along every axis the direction crosses, leave
 // through the same event with the same exit-table entries, and cross segments
 // of the same lengths whose tile offsets are negatives of each other.  So one
-// thread marches both in lockstep from one event list, with the two
-// exponentials' arithmetic on packed FP32 pairs (f32x2), and only the
-// in-plane face coordinates (which may differ along an axis the direction
-// does not cross) and the staged faces are per ray.  The cell order lists
-// the pairs (d, -d) consecutively; a staged tile holds dt / 2 pairs.
+// thread marches both in lockstep from one event list and one 16-byte load
+// of the paired tile per step, with the two exponentials' arithmetic on
+// packed FP32 pairs (f32x2); only the in-plane face coordinates (which may
+// differ along an axis the direction does not cross) and the staged faces
+// are per ray.  The lanes of a warp march aligned at the downwind end, as in
+// the face pass, so that at each step they read one event and a brick of
+// neighbouring entries.  The cell order lists the pairs (d, -d)
+// consecutively; a staged tile holds dt / 2 pairs.
 // one lower-half cell and its mirror per thread; 512 threads (two CTAs per SM)
 // for 16^3 blocks, where three 256-thread CTAs would hold fewer warps
 __host__ __device__ constexpr int pair_threads(int B) { return B == 16 ? 512 : 256; }
@@ -642,46 +650,76 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
   return d;
 }
 
-// One segment of both rays: t1, t2 are the byte addresses of the rays' start
-// cells in the (kappa, S) tile; the mirror ray moves by -off.  The same update
-// and the same two forms as segment().
-__device__ __forceinline__ void segment_pair(const unsigned char *__restrict__ t1, const unsigned char *__restrict__ t2,
-                                             const TplEvent<float> &ev, uint64_t &I) {
-  const float2 ks1 = *reinterpret_cast<const float2 *>(t1 + ev.off);  // (kappa, S): one 8-byte load
-  const float2 ks2 = *reinterpret_cast<const float2 *>(t2 - ev.off);
-  const float s1 = ks1.y, s2 = ks2.y;
-  const uint64_t Y = mul2(pk2(ks1.x, ks2.x), pk2(ev.len, ev.len));
-  float y1, y2;
-  upk2(Y, y1, y2);
-  float e1, e2;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(y1));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(y2));
-  uint64_t q = pk2(1.0833843353054956e-03f, 1.0833843353054956e-03f);
-  q = fma2(q, Y, pk2(9.4645342235962007e-03f, 9.4645342235962007e-03f));
-  q = fma2(q, Y, pk2(5.5464640186780434e-02f, 5.5464640186780434e-02f));
-  q = fma2(q, Y, pk2(2.4022290282685121e-01f, 2.4022290282685121e-01f));
-  q = fma2(q, Y, pk2(6.9314712699664371e-01f, 6.9314712699664371e-01f));
-  float n1, n2;  // -(1 - e^-x) of the thin form
-  upk2(mul2(q, Y), n1, n2);
-  const bool thin1 = y1 > -0.7213475204444817f, thin2 = y2 > -0.7213475204444817f;
-  float i1, i2;
-  upk2(I, i1, i2);
-  I = fma2(sub2(I, pk2(s1, s2)), pk2(thin1 ? n1 : e1, thin2 ? n2 : e2), pk2(thin1 ? i1 : s1, thin2 ? i2 : s2));
+// The paired tiles of both mirrored passes hold 16-byte entries (kappa(p),
+// kappa(p'), S(p), S(p')): p' is the cell where the mirror ray stands when
+// the primary ray stands at p.  Template offsets are for 8-byte entries,
+// hence 2 * off below.
+
+// One ray on a paired tile, on a template of its own (a pair whose templates
+// are not exact mirrors): march() reading the ray's own (kappa, S) = (.x, .z).
+__device__ __forceinline__ float march4(const unsigned char *__restrict__ tb, int last,
+                                       const TplEvent<float> *__restrict__ ev, float I) {
+  for (int e = last; e >= 0; --e) {
+    const TplEvent<float> E = ev[e];
+    const float4 q = *reinterpret_cast<const float4 *>(tb + 2 * E.off);
+    bool thin;
+    const float w = seg_weight(q.x * E.len, thin);
+    I = fmaf(I - q.z, w, thin ? I : q.z);
+  }
+  return I;
 }
 
 // One cell ray on its own template (upwind-frame coordinates l0..l2, start
-// cell at byte address tb in the tile): exit lookup, entry value, march.
-template <typename R>
-__device__ __forceinline__ R cell_ray(const Tpl<R> &T, const R *fin, int fstride, int B, int l0, int l1, int l2,
-                                      const vec2_t<R> *tile, const unsigned char *tb) {
+// entry at byte address tb of the paired tile): exit lookup, entry value,
+// march.
+__device__ __forceinline__ float cell_ray4(const Tpl<float> &T, const float *fin, int fstride, int B, int l0, int l1,
+                                           int l2, const unsigned char *tb) {
   const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
   int last = p0, ae = 0, la = l0, lb = l1, lc = l2;
   if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; }
   if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; }
   const int row = (ae * 2) * B + la;
-  const R Iin = face_value<R>(fin, fstride, B, ae, lb, lc, T.ck[row], T.ck[row + B], T.cw[row], T.cw[row + B]);
-  const int idx0 = (int)((tb - reinterpret_cast<const unsigned char *>(tile)) / (long long)sizeof(vec2_t<R>));
-  return march<R>(tile, idx0, last, T.cev, Iin);
+  const float Iin = face_value<float>(fin, fstride, B, ae, lb, lc, T.ck[row], T.ck[row + B], T.cw[row], T.cw[row + B]);
+  return march4(tb, last, T.cev, Iin);
+}
+
+// Paired tile of the cell pass: p' is the point-mirrored cell of the same block.
+template <int BC>
+__device__ __forceinline__ void load_tile_pair(float4 *tile, TileShape ts, const GridDims &g, int bx, int by, int bz,
+                                               const float *__restrict__ kappa, const float *__restrict__ S) {
+  constexpr int B = BC, B2 = B * B, B3 = B2 * B;
+  for (int i = threadIdx.x; i < B3; i += blockDim.x) {
+    const int x = i % B, y = (i / B) % B, z = i / B2;
+    const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
+    const long long gm = ((long long)(bz * B + B - 1 - z) * g.ny + (by * B + B - 1 - y)) * g.nx + (bx * B + B - 1 - x);
+    tile[x + ts.sy * y + ts.sz * z] = make_float4(kappa[gi], kappa[gm], S[gi], S[gm]);
+  }
+}
+
+// One segment of both rays of a mirrored pair on a paired tile (tb: the
+// primary ray's start entry): the update and the two forms of segment() on
+// packed FP32 pairs.
+__device__ __forceinline__ void segment_pair_tile(const unsigned char *__restrict__ tb, const TplEvent<float> &ev,
+                                                  uint64_t &I) {
+  const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(tb + 2 * ev.off);  // (k, k'), (S, S')
+  const uint64_t Y = mul2(q.x, pk2(ev.len, ev.len));
+  float y1, y2;
+  upk2(Y, y1, y2);
+  float e1, e2;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(y1));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(y2));
+  uint64_t p = pk2(1.0833843353054956e-03f, 1.0833843353054956e-03f);
+  p = fma2(p, Y, pk2(9.4645342235962007e-03f, 9.4645342235962007e-03f));
+  p = fma2(p, Y, pk2(5.5464640186780434e-02f, 5.5464640186780434e-02f));
+  p = fma2(p, Y, pk2(2.4022290282685121e-01f, 2.4022290282685121e-01f));
+  p = fma2(p, Y, pk2(6.9314712699664371e-01f, 6.9314712699664371e-01f));
+  float n1, n2;  // -(1 - e^-x) of the thin form
+  upk2(mul2(p, Y), n1, n2);
+  const bool thin1 = y1 > -0.7213475204444817f, thin2 = y2 > -0.7213475204444817f;
+  float i1, i2, s1, s2;
+  upk2(I, i1, i2);
+  upk2(q.y, s1, s2);
+  I = fma2(sub2(I, q.y), pk2(thin1 ? n1 : e1, thin2 ? n2 : e2), pk2(thin1 ? i1 : s1, thin2 ? i2 : s2));
 }
 
 template <int MODE, int BC>
@@ -698,8 +736,8 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
   const TplLayout TL = tpl_layout<float>(B);
   const int fstride = g.fstride;
   const size_t sb = slot_bytes<float>(B);
-  float2 *tile = reinterpret_cast<float2 *>(smem);
-  unsigned char *buf0 = smem + align16(sizeof(float2) * (size_t)ts.elems);
+  float4 *tile = reinterpret_cast<float4 *>(smem);
+  unsigned char *buf0 = smem + align16(sizeof(float4) * (size_t)ts.elems);
   const int item = blockIdx.x / parts, part = blockIdx.x - item * parts;
   const int blk = block_list ? block_list[item] : item;
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
@@ -723,7 +761,7 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     issue_tile(0);
     if (ntiles > 1) issue_tile(1);
   }
-  load_tile<float, BC>(tile, ts, g, bx, by, bz, kappa, S);
+  load_tile_pair<BC>(tile, ts, g, bx, by, bz, kappa, S);
   __syncthreads();
 
   // this thread's lower-half cell (z < B/2): 4 x 4 x 2 bricks, warp-major
@@ -786,20 +824,22 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
         const float Iin1 = face_value<float>(fin1, fstride, B, ae, lb, lc, kb, kc, wb, wc);
         const float Iin2 = face_value<float>(fin2, fstride, B, ae, nb_, nc_, kb, kc, wb, wc);
         uint64_t I = pk2(Iin1, Iin2);
-        int e = last;
+        int e = __reduce_max_sync(0xffffffffu, last);
         for (; e > 0; e -= 2) {
-          const TplEvent<float> e0 = T.cev[e], e1 = T.cev[e - 1];
-          segment_pair(t1, t2, e0, I);
-          segment_pair(t1, t2, e1, I);
+          TplEvent<float> e0 = T.cev[e], e1 = T.cev[e - 1];
+          if (e > last) { e0.len = 0.f; e0.off = 0; }
+          if (e - 1 > last) { e1.len = 0.f; e1.off = 0; }
+          segment_pair_tile(t1, e0, I);
+          segment_pair_tile(t1, e1, I);
         }
-        if (e == 0) segment_pair(t1, t2, T.cev[0], I);
+        if (e == 0) segment_pair_tile(t1, T.cev[0], I);
         upk2(I, I1, I2);
       } else {
         // the pair's templates differ (near-tied plane crossings ordered
         // differently): each ray follows its own direction's template
         const Tpl<float> T2(buf + sb * j2, TL);
-        I1 = cell_ray<float>(T, fin1, fstride, B, l0, l1, l2, tile, t1);
-        I2 = cell_ray<float>(T2, fin2, fstride, B, m0, m1, m2, tile, t2);
+        I1 = cell_ray4(T, fin1, fstride, B, l0, l1, l2, t1);
+        I2 = cell_ray4(T2, fin2, fstride, B, m0, m1, m2, t2);
       }
       if (MODE == 1) {
         I_out[(long long)T.h->ext * g.ncell + gc1] = I1;
@@ -885,31 +925,6 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
 // with p' the mirrored cell, so each step of a ray pair is one 16-byte load
 // already packed for the f32x2 arithmetic.  Only the staged incoming faces
 // differ between the two rays of a pair.
-
-// One segment of both rays on the paired tile (tb: the primary ray's start
-// entry; template offsets are for 8-byte entries, hence 2 * off).
-__device__ __forceinline__ void segment_pair_tile(const unsigned char *__restrict__ tb, const TplEvent<float> &ev,
-                                                  uint64_t &I) {
-  const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(tb + 2 * ev.off);  // (k, k'), (S, S')
-  const uint64_t Y = mul2(q.x, pk2(ev.len, ev.len));
-  float y1, y2;
-  upk2(Y, y1, y2);
-  float e1, e2;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(y1));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(y2));
-  uint64_t p = pk2(1.0833843353054956e-03f, 1.0833843353054956e-03f);
-  p = fma2(p, Y, pk2(9.4645342235962007e-03f, 9.4645342235962007e-03f));
-  p = fma2(p, Y, pk2(5.5464640186780434e-02f, 5.5464640186780434e-02f));
-  p = fma2(p, Y, pk2(2.4022290282685121e-01f, 2.4022290282685121e-01f));
-  p = fma2(p, Y, pk2(6.9314712699664371e-01f, 6.9314712699664371e-01f));
-  float n1, n2;  // -(1 - e^-x) of the thin form
-  upk2(mul2(p, Y), n1, n2);
-  const bool thin1 = y1 > -0.7213475204444817f, thin2 = y2 > -0.7213475204444817f;
-  float i1, i2, s1, s2;
-  upk2(I, i1, i2);
-  upk2(q.y, s1, s2);
-  I = fma2(sub2(I, q.y), pk2(thin1 ? n1 : e1, thin2 ? n2 : e2), pk2(thin1 ? i1 : s1, thin2 ? i2 : s2));
-}
 
 template <int BC>
 __device__ __forceinline__ void load_tile_mirrored(float4 *tile, TileShape ts, const GridDims &g, int bx, int by,
@@ -1185,7 +1200,7 @@ void pair_launch(const GridDims &g, const float *kappa, const float *S, const un
   const int parts = BC * BC * BC / 2 / pair_threads(BC);
   const int nblk = block_list ? nlist : g.nbx * g.nby * g.nbz;
   const int dt = pair_dir_tile(BC, g.dir_tile);
-  cell_pair_kernel<MODE, BC><<<nblk * parts, pair_threads(BC), smem_bytes<float>(BC, 2 * dt), st>>>(
+  cell_pair_kernel<MODE, BC><<<nblk * parts, pair_threads(BC), pair_smem_bytes(BC, 2 * dt), st>>>(
       g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, status,
       block_list);
 }
