@@ -270,9 +270,30 @@ __host__ __device__ inline size_t face_slot_bytes_t(int B) {
   return (size_t)tpl_layout<R>(B).node_bytes + faces_bytes<R>(B);
 }
 
-template <typename R, int BC>
+// Tile loaders.  With the block edge and the CTA's thread count known at
+// compile time (NT != 0) every thread issues all its global loads before its
+// first shared-memory store, so they are in flight together.
+template <typename R, int BC, int NT = 0>
 __device__ __forceinline__ void load_tile(vec2_t<R> *tile, TileShape ts, const GridDims &g, int bx, int by, int bz,
                                           const R *__restrict__ kappa, const R *__restrict__ S) {
+  if constexpr (BC != 0 && NT != 0) {
+    constexpr int B = BC, B2 = B * B, K = B2 * B / NT;
+    static_assert(B2 * B % NT == 0, "tile cells must divide evenly over the threads");
+    vec2_t<R> v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = (int)threadIdx.x + k * NT, x = i % B, y = (i / B) % B, z = i / B2;
+      const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
+      v[k].x = kappa[gi];
+      v[k].y = S[gi];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = (int)threadIdx.x + k * NT, x = i % B, y = (i / B) % B, z = i / B2;
+      tile[x + ts.sy * y + ts.sz * z] = v[k];
+    }
+    return;
+  }
   const int B = BC ? BC : g.B;
   const int B2 = B * B, B3 = B2 * B;
   for (int i = threadIdx.x; i < B3; i += blockDim.x) {
@@ -355,7 +376,7 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
     for (int j = 0; j < it.dir_count; ++j)
       issue_slot<R>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full, TL.node_bytes);
   }
-  load_tile<R, BC>(tile, ts, g, bx, by, bz, kappa, S);
+  load_tile<R, BC, kFaceThreads>(tile, ts, g, bx, by, bz, kappa, S);
   __syncthreads();
   if (!mbar_wait_warp(&full, 0, spin_limit, status, 1)) {
     // the copies this CTA issued must land before its shared memory is
@@ -683,7 +704,9 @@ __device__ __forceinline__ float cell_ray4(const Tpl<float> &T, const float *fin
   return march4(tb, last, T.cev, Iin);
 }
 
-// Paired tile of the cell pass: p' is the point-mirrored cell of the same block.
+// Paired tile of the cell pass: p' is the point-mirrored cell of the same
+// block.  (Issuing all loads before the stores, as the face passes do, made
+// this kernel slower.)
 template <int BC>
 __device__ __forceinline__ void load_tile_pair(float4 *tile, TileShape ts, const GridDims &g, int bx, int by, int bz,
                                                const float *__restrict__ kappa, const float *__restrict__ S) {
@@ -926,17 +949,27 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
 // already packed for the f32x2 arithmetic.  Only the staged incoming faces
 // differ between the two rays of a pair.
 
-template <int BC>
+// Paired tile of the face pass: p' is the point-mirrored cell of block
+// (mx, my, mz) (NT threads, all loads in flight before the stores).
+template <int BC, int NT>
 __device__ __forceinline__ void load_tile_mirrored(float4 *tile, TileShape ts, const GridDims &g, int bx, int by,
                                                    int bz, int mx, int my, int mz, const float *__restrict__ kappa,
                                                    const float *__restrict__ S) {
-  constexpr int B = BC, B2 = B * B, B3 = B2 * B;
-  for (int i = threadIdx.x; i < B3; i += blockDim.x) {
-    const int x = i % B, y = (i / B) % B, z = i / B2;
+  constexpr int B = BC, B2 = B * B, K = B2 * B / NT;
+  static_assert(B2 * B % NT == 0, "tile cells must divide evenly over the threads");
+  float4 v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int i = (int)threadIdx.x + k * NT, x = i % B, y = (i / B) % B, z = i / B2;
     const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
     const long long gm =
         ((long long)(mz * B + B - 1 - z) * g.ny + (my * B + B - 1 - y)) * g.nx + (mx * B + B - 1 - x);
-    tile[x + ts.sy * y + ts.sz * z] = make_float4(kappa[gi], kappa[gm], S[gi], S[gm]);
+    v[k] = make_float4(kappa[gi], kappa[gm], S[gi], S[gm]);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int i = (int)threadIdx.x + k * NT, x = i % B, y = (i / B) % B, z = i / B2;
+    tile[x + ts.sy * y + ts.sz * z] = v[k];
   }
 }
 
@@ -979,7 +1012,7 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
                         &full, 0);
     }
   }
-  load_tile_mirrored<BC>(tile, ts, g, bx, by, bz, mx, my, mz, kappa, S);
+  load_tile_mirrored<BC, kFaceThreads>(tile, ts, g, bx, by, bz, mx, my, mz, kappa, S);
   __syncthreads();
   if (!mbar_wait_warp(&full, 0, spin_limit, status, 1)) {
     if (threadIdx.x == 0) mbar_wait(&full, 0, kDrainPolls, status, 8);
