@@ -258,6 +258,38 @@ inline bool antipodal_order(int N, const double *dirs, const int *order, int *ou
   return ok;
 }
 
+// Exit tables of two templates with the same event positions pos[3][rows]:
+// equal (floor, fraction within 1e-6) on every row a ray can exit through.
+// A ray exits by the plane event that comes first along its three axes, so
+// row (a, l) is read only if pos[a][l] is below the latest event of each
+// other axis; the other rows (planes the direction would cross only beyond
+// the block, as along an axis with a component near zero, whose far-off
+// tables differ in rounding between a direction and its antipode) are never
+// read.
+template <typename R>
+inline bool exit_rows_match(const int16_t *pos, const unsigned char *ka, const unsigned char *wa,
+                            const unsigned char *kb, const unsigned char *wb, int rows) {
+  const int16_t *Ka = reinterpret_cast<const int16_t *>(ka), *Kb = reinterpret_cast<const int16_t *>(kb);
+  const R *Wa = reinterpret_cast<const R *>(wa), *Wb = reinterpret_cast<const R *>(wb);
+  int latest[3];
+  for (int a = 0; a < 3; ++a) {
+    latest[a] = pos[a * rows];
+    for (int l = 1; l < rows; ++l) latest[a] = std::max(latest[a], (int)pos[a * rows + l]);
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int l = 0; l < rows; ++l) {
+      const int p = pos[a * rows + l];
+      if (p == kNever || p > latest[(a + 1) % 3] || p > latest[(a + 2) % 3]) continue;
+      for (int j = 0; j < 2; ++j) {
+        const int idx = (a * 2 + j) * rows + l;
+        if (Ka[idx] != Kb[idx]) return false;
+        if (std::fabs((double)Wa[2 * idx] - (double)Wb[2 * idx]) > 1e-6) return false;
+        if (std::fabs((double)Wa[2 * idx + 1] - (double)Wb[2 * idx + 1]) > 1e-6) return false;
+      }
+    }
+  return true;
+}
+
 // Mirrored octant order for the paired face pass: within octant 7 - o (the
 // antipodes of octant o, o with a non-negative x component), internal
 // direction ob[7 - o] + k becomes the antipode of ob[o] + k.  Requires every
@@ -304,17 +336,14 @@ inline bool mirror_node_templates(const unsigned char *ta, const unsigned char *
     if (std::fabs(la - lb) > 1e-6 * std::fabs(la)) return false;
   }
   if (std::memcmp(ta + L.npos, tb + L.npos, 3 * (B + 1) * 2) != 0) return false;
-  if (std::memcmp(ta + L.nk, tb + L.nk, 6 * (B + 1) * 2) != 0) return false;
-  const R *wa = reinterpret_cast<const R *>(ta + L.nw), *wb = reinterpret_cast<const R *>(tb + L.nw);
-  for (int i = 0; i < 6 * (B + 1) * 2; ++i)
-    if (std::fabs((double)wa[i] - (double)wb[i]) > 1e-6) return false;
-  return true;
+  return exit_rows_match<R>(reinterpret_cast<const int16_t *>(ta + L.npos), ta + L.nk, ta + L.nw, tb + L.nk,
+                            tb + L.nw, B + 1);
 }
 
 // Whether the cell-ray parts of two templates (of antipodal directions) are
 // exact mirror images: equal event lengths (relative 1e-6) with negated
-// offsets, zero-length tie segments aside, and identical exit-event and
-// exit tables.  Near-ties of plane crossings (|n_a| equal to the last bit, as on
+// offsets, zero-length tie segments aside, identical exit-event tables, and
+// equal exit tables on the rows a ray can exit through.  Near-ties of plane crossings (|n_a| equal to the last bit, as on
 // the unrotated HEALPix rings at 45 degrees) can be ordered differently for
 // a direction and its antipode; such pairs fail the test.
 template <typename R>
@@ -333,11 +362,8 @@ inline bool mirror_templates(const unsigned char *ta, const unsigned char *tb, i
     if (std::fabs(la - lb) > 1e-6 * std::fabs(la)) return false;
   }
   if (std::memcmp(ta + L.cpos, tb + L.cpos, 3 * B * 2) != 0) return false;
-  if (std::memcmp(ta + L.ck, tb + L.ck, 6 * B * 2) != 0) return false;
-  const R *wa = reinterpret_cast<const R *>(ta + L.cw), *wb = reinterpret_cast<const R *>(tb + L.cw);
-  for (int i = 0; i < 6 * B * 2; ++i)
-    if (std::fabs((double)wa[i] - (double)wb[i]) > 1e-6) return false;
-  return true;
+  return exit_rows_match<R>(reinterpret_cast<const int16_t *>(ta + L.cpos), ta + L.ck, ta + L.cw, tb + L.ck,
+                            tb + L.cw, B);
 }
 
 // Face-pass schedule: level L of block b in octant o is b's upwind-ordered

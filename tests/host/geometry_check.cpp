@@ -1,0 +1,102 @@
+// Host-side checks of the mirrored-pair bookkeeping in vet_geometry.h (no GPU):
+//  - mirror_octant_order puts antipodes at equal positions of opposite octants;
+//  - the cell- and node-ray parts of each antipodal pair's templates are
+//    exact mirrors (rotated sets), and a template is not the mirror of a
+//    direction other than its antipode;
+//  - the paired face-pass schedule, with each item's point-mirrored block and
+//    antipodal directions added, lists every (block, direction) of the
+//    unpaired schedule exactly once, level by level.
+// Usage: geometry_check nbx nby nbz B nside [unrotated]   (prints "ok" or the
+// failure).  The rotation is a generic one (irrational components: no two
+// plane crossings of a direction tie); "unrotated" checks instead that the
+// HEALPix set itself, with its z = 0 ring, is refused.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <set>
+#include <tuple>
+#include <vector>
+
+#include "vet_geometry.h"
+
+static int fail(const char *what) {
+  std::printf("FAIL: %s\n", what);
+  return 1;
+}
+
+int main(int argc, char **argv) {
+  if (argc != 6 && argc != 7) return fail("usage");
+  const int nb[3] = {std::atoi(argv[1]), std::atoi(argv[2]), std::atoi(argv[3])};
+  const int B = std::atoi(argv[4]), nside = std::atoi(argv[5]), N = 12 * nside * nside;
+  const bool unrotated = argc == 7;
+  double q[4] = {std::sqrt(0.5), 1.0 / std::sqrt(10.0), 1.0 / std::sqrt(3.0), 0.2};
+  if (unrotated) q[0] = 1.0, q[1] = q[2] = q[3] = 0.0;
+  const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (double &x : q) x /= qn;
+  std::vector<double> d(4 * N);
+  vet::geom::healpix_directions(nside, q, d.data());
+  std::vector<int> order(N);
+  int ob[9];
+  vet::geom::internal_order(N, d.data(), order.data(), ob);
+  if (unrotated) {
+    const std::vector<int> before = order;
+    if (vet::geom::mirror_octant_order(N, d.data(), order.data(), ob)) return fail("a set with zero components was paired");
+    if (order != before) return fail("a refused mirror order changed the order");
+    std::printf("ok\n");
+    return 0;
+  }
+  if (!vet::geom::mirror_octant_order(N, d.data(), order.data(), ob)) return fail("mirror_octant_order refused a rotated set");
+  for (int o = 0; o < 8; o += 2)
+    for (int k = 0; k < ob[o + 1] - ob[o]; ++k) {
+      const double *a = &d[4 * order[ob[o] + k]], *b = &d[4 * order[ob[7 - o] + k]];
+      if (std::fabs(a[0] + b[0]) + std::fabs(a[1] + b[1]) + std::fabs(a[2] + b[2]) > 1e-12)
+        return fail("octant positions do not hold antipodes");
+    }
+  const int tb = vet::tpl_layout<float>(B).bytes;
+  std::vector<unsigned char> tpl((size_t)tb * N);
+  for (int i = 0; i < N; ++i) {
+    long long cs, ns[3];
+    vet::geom::build_template<float>(&d[4 * order[i]], order[i], B, 0.01, tpl.data() + (size_t)i * tb, cs, ns);
+  }
+  auto T = [&](int i) { return tpl.data() + (size_t)i * tb; };
+  for (int o = 0; o < 8; o += 2)
+    for (int k = 0; k < ob[o + 1] - ob[o]; ++k) {
+      const int i = ob[o] + k, j = ob[7 - o] + k;
+      if (!vet::geom::mirror_node_templates<float>(T(i), T(j), B)) return fail("node rays of an antipodal pair");
+      if (!vet::geom::mirror_templates<float>(T(i), T(j), B)) return fail("cell rays of an antipodal pair");
+      const int other = ob[7 - o] + (k + 1) % (ob[o + 1] - ob[o]);
+      if (other != j && vet::geom::mirror_node_templates<float>(T(i), T(other), B))
+        return fail("a non-antipodal pair passed the node mirror check");
+    }
+  const int nl = nb[0] + nb[1] + nb[2] - 2;
+  for (int g : {1, 2, 4, 8}) {
+    std::vector<int> off(nl + 1), poff(nl + 1);
+    const long long nu = vet::geom::build_schedule(nb, ob, g, nullptr, 1LL << 40, off.data());
+    std::vector<vet::FaceItem> U((size_t)nu + 1);
+    vet::geom::build_schedule(nb, ob, g, U.data(), nu, off.data());
+    const long long np = vet::geom::build_schedule(nb, ob, g, nullptr, 1LL << 40, poff.data(), nullptr, true);
+    std::vector<vet::FaceItem> P((size_t)np + 1);
+    vet::geom::build_schedule(nb, ob, g, P.data(), np, poff.data(), nullptr, true);
+    for (int L = 0; L < nl; ++L) {
+      std::multiset<std::tuple<int, int>> a, b;
+      for (int i = off[L]; i < off[L + 1]; ++i)
+        for (int j = 0; j < U[i].dir_count; ++j) a.insert({U[i].block, U[i].dir_begin + j});
+      for (int i = poff[L]; i < poff[L + 1]; ++i) {
+        const int bx = P[i].block % nb[0], by = (P[i].block / nb[0]) % nb[1], bz = P[i].block / (nb[0] * nb[1]);
+        const int mb = ((nb[2] - 1 - bz) * nb[1] + (nb[1] - 1 - by)) * nb[0] + (nb[0] - 1 - bx);
+        if (P[i].dir_count > g) return fail("paired item larger than its group");
+        for (int j = 0; j < P[i].dir_count; ++j) {
+          b.insert({P[i].block, P[i].dir_begin + j});
+          b.insert({mb, P[i].mirror_begin + j});
+          const double *x = &d[4 * order[P[i].dir_begin + j]], *y = &d[4 * order[P[i].mirror_begin + j]];
+          if (std::fabs(x[0] + y[0]) + std::fabs(x[1] + y[1]) + std::fabs(x[2] + y[2]) > 1e-12)
+            return fail("paired item's mirror directions are not antipodes");
+        }
+      }
+      if (a != b) return fail("paired schedule does not cover the unpaired one");
+    }
+    if (2 * np != nu) return fail("paired schedule is not half the unpaired one");
+  }
+  std::printf("ok\n");
+  return 0;
+}

@@ -98,15 +98,27 @@ def test_fp64_trace_and_closure_match_oracle(ora, case):
 
 
 # --------------------------------------------------------------- FP32 path
+# a rotation that takes one nside = 8 direction to |n_y| = 6.4e-6: its exits
+# through y planes lie far beyond any block, and the mirrored passes must not
+# let the never-read exit-table rows for them decide whether a pair mirrors
+NEAR_PLANE_Q = np.array([np.sqrt(0.5), 1 / np.sqrt(10.0), 1 / np.sqrt(3.0), 0.2])
+
+
 @pytest.mark.parametrize("case", ["blob32", "lognormal48", "cloud", "ragged", "tiny_blocks", "unrotated8",
-                                  "unrotated16"])
+                                  "unrotated16", "near_plane8", "near_plane16"])
 def test_fp32_closure_matches_oracle(ora, case):
     """The unrotated cases hold directions with an exactly zero component (the
     HEALPix equator ring, n_z = 0), where a direction and its antipode both
     count the zero axis as positive: the paired cell pass must then take the
-    in-plane face coordinates of each ray from its own direction."""
+    in-plane face coordinates of each ray from its own direction, and the
+    face pass runs unpaired."""
     Ib = None
-    if case == "unrotated8":
+    if case.startswith("near_plane"):
+        B = 8 if case == "near_plane8" else 16
+        p = synth.lognormal_problem(shape=(16, 16, 32), B=B, nside=8, seed=26)
+        p["q"] = NEAR_PLANE_Q / np.linalg.norm(NEAR_PLANE_Q)
+        Ib = np.random.default_rng(26).uniform(0, 0.5, (6, 768))
+    elif case == "unrotated8":
         p = synth.blob_problem(n=16, B=8, nside=2, seed=1, rotate=False)
         Ib = np.random.default_rng(24).uniform(0, 0.5, (6, 48))
     elif case == "unrotated16":
