@@ -150,6 +150,22 @@ def test_fp32_closure_matches_oracle(ora, case):
     assert f_error(f, f_ref, M_ref) < FTOL32
 
 
+@pytest.mark.parametrize("seed", [101, 102, 103, 104, 105, 106])
+def test_fp32_closure_matches_oracle_on_random_rotations(ora, seed):
+    """Haar-random rotations of the nside = 4 set: whichever direction pairs
+    the host finds to be exact mirrors run paired, the others ray by ray."""
+    B = 8 if seed % 2 else 16
+    p = synth.lognormal_problem(shape=(16, 32, 32), B=B, nside=4, seed=seed)
+    Ib = np.random.default_rng(seed).uniform(0, 0.5, (6, 192))
+    ctx = _ctx(p, vet.VET_FP32)
+    dev_in, host_in = _inputs(p, np.float32, Ib)
+    f_ref, M_ref, _, _ = ora.vet_closure(host_in[0], host_in[1], ctx.directions(), p["B"], p["h"], host_in[2])
+    f, M = _gpu_closure(ctx, dev_in, f_ref[0].size, np.float32)
+    eE, eFP = moment_errors(M, M_ref)
+    assert eE < RTOL32 and eFP < RTOL32, (eE, eFP)
+    assert f_error(f, f_ref, M_ref) < FTOL32
+
+
 def test_fp32_moments_entry_point_matches_oracle(ora):
     p = synth.lognormal_problem(n=16, B=8, nside=2, seed=31)
     ctx = _ctx(p, vet.VET_FP32)
