@@ -847,13 +847,28 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
         const float Iin1 = face_value<float>(fin1, fstride, B, ae, lb, lc, kb, kc, wb, wc);
         const float Iin2 = face_value<float>(fin2, fstride, B, ae, nb_, nc_, kb, kc, wb, wc);
         uint64_t I = pk2(Iin1, Iin2);
+        // aligned at the downwind end; once the event index reaches the
+        // warp's smallest `last` every lane marches and the identity
+        // selects are dropped (the face passes, whose warps more often mix
+        // templates and upwind-face nodes, measured slower with this split)
         int e = __reduce_max_sync(0xffffffffu, last);
-        for (; e > 0; e -= 2) {
+        const int wmin = __reduce_min_sync(0xffffffffu, last);
+        for (; e - 1 > wmin; e -= 2) {  // some lanes not yet started
           TplEvent<float> e0 = T.cev[e], e1 = T.cev[e - 1];
           if (e > last) { e0.len = 0.f; e0.off = 0; }
           if (e - 1 > last) { e1.len = 0.f; e1.off = 0; }
           segment_pair_tile(t1, e0, I);
           segment_pair_tile(t1, e1, I);
+        }
+        if (e > wmin) {
+          TplEvent<float> e0 = T.cev[e];
+          if (e > last) { e0.len = 0.f; e0.off = 0; }
+          segment_pair_tile(t1, e0, I);
+          --e;
+        }
+        for (; e > 0; e -= 2) {  // every lane marching
+          segment_pair_tile(t1, T.cev[e], I);
+          segment_pair_tile(t1, T.cev[e - 1], I);
         }
         if (e == 0) segment_pair_tile(t1, T.cev[0], I);
         upk2(I, I1, I2);
