@@ -14,6 +14,9 @@ The line also carries, at N = 1, a "learned" object: the learned closure
 (network + indicator + exact fallback on flagged blocks) at 256^3 against the
 plain closure on the same GPU, with the network trained in the same run.
 
+It also carries, at N = 1, a "batch" object: 64 ragged grids as one batched
+closure (one CUDA graph) against the same closures launched one by one.
+
 Prints one JSON line on rank 0.  With --gpus N > 1 (under torchrun) every
 rank runs an independent replica of the workload on its own GPU (the method
 has no data exchange between replicas); the value is the total over ranks
@@ -176,6 +179,49 @@ def conv_flops_per_cell():
     """Multiply-adds x 2 of the four convolutions as stored (padded channels:
     16 -> 32 -> 32 -> 32 -> 16)."""
     return 2 * 27 * (16 * 32 + 32 * 32 + 32 * 32 + 32 * 16)
+
+
+def batch_measurement(local_rank, reps: int = 20):
+    """64 ragged grids (edges 32..96, block edges 8 and 16, nside 2 and 4,
+    lognormal fields; synth.batched_problems) as one batched closure (one
+    CUDA graph, tiles autotuned per grid shape) against the same grids'
+    closures launched one after another, inputs resident in HBM."""
+    import numpy as np
+    import torch
+
+    from paper_2202_08778_gb300 import synth, vet
+
+    dev = torch.device("cuda", local_rank)
+    probs = synth.batched_problems(n_grids=64, seed0=100)
+    k = [torch.from_numpy(p["kappa"].astype(np.float32)).to(dev) for p in probs]
+    s = [torch.from_numpy(p["S"].astype(np.float32)).to(dev) for p in probs]
+    f = [torch.empty(6 * p["kappa"].size, dtype=torch.float32, device=dev) for p in probs]
+    b = vet.Batch([(p["kappa"].shape, p["B"], p["h"], p["nside"], p["q"]) for p in probs], device=local_rank)
+    b.autotune(k, s)
+    updates = sum(p["kappa"].size * 12 * p["nside"] ** 2 for p in probs)
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n
+
+    def sequential():
+        for i, c in enumerate(b.members):
+            c.closure(k[i], s[i], None, f[i])
+
+    t_batch = timed(lambda: b.closure(k, s, None, f), reps)
+    b.sync()
+    t_seq = timed(sequential, max(3, reps // 4))
+    return {"workload": "64 ragged lognormal grids (synth.batched_problems, seed0 100)", "grids": len(probs),
+            "ms": t_batch, "value": updates / (t_batch * 1e-3) / 1e9, "unit": UNIT, "ms_sequential": t_seq,
+            "speedup_vs_sequential": t_seq / t_batch}
 
 
 def learned_measurement(local_rank):
@@ -386,6 +432,9 @@ def run_ours(args, rank, world, local_rank):
     if clocks is not None:
         line["clocks"] = clocks
 
+    if rank == 0 and world == 1 and not args.no_batch:
+        line["batch"] = batch_measurement(local_rank)
+
     if rank == 0 and world == 1 and not args.no_learned:
         line["learned"] = learned_measurement(local_rank)
 
@@ -407,6 +456,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-grid batched-closure measurement")
     ap.add_argument("--tuning", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
                     metavar="FG,DT", help="fixed face-pass direction group and cell-pass direction tile "
                     "instead of autotuning")

@@ -612,8 +612,9 @@ __global__ void __launch_bounds__(kCellThreads, 2)
         E_out[gc] = E;
       }
       if (E > R(0)) {
-        const R inv = R(1) / E;
-        for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = mom[4 + m] * inv;
+        // f = P / E correctly rounded (IEEE division; for FP32 operands the
+        // same value as the FP64 quotient rounded to FP32)
+        for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = mom[4 + m] / E;
       } else {
         for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = m < 3 ? R(1) / R(3) : R(0);
       }
@@ -938,8 +939,8 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
           E_out[gc] = E;
         }
         if (E > 0.f) {
-          const float inv = 1.f / E;
-          for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = mom[r][4 + m] * inv;
+          // correctly rounded, as in cell_pass_kernel
+          for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = mom[r][4 + m] / E;
         } else {
           for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = m < 3 ? 1.f / 3.f : 0.f;
         }
