@@ -459,6 +459,21 @@ class Model:
         self._check(self._lib.vet_model_get_grads(self._h, flat.ctypes.data))
         return self._unflat(flat)
 
+    def save(self, path):
+        """Write the FP32 parameters (per layer W [27][C_out][C_in], b [C_out])
+        to an .npz file."""
+        arrays = {}
+        for i, (W, b) in enumerate(self.params()):
+            arrays[f"W{i}"], arrays[f"b{i}"] = W, b
+        np.savez(path, channels=np.int32(self.channels), **arrays)
+
+    def load(self, path):
+        """Read parameters written by save() (the hidden width must match)."""
+        with np.load(path) as z:
+            if int(z["channels"]) != self.channels:
+                raise ValueError(f"file has {int(z['channels'])} hidden channels, model has {self.channels}")
+            self.set_params([(z[f"W{i}"], z[f"b{i}"]) for i in range(len(self.shapes))])
+
     def features(self, shape, block: int, h: float, kappa, S, E, nvol: int = 1, feat_out=None, stream=None):
         """Features of nvol stacked volumes of `shape` (device tensors)."""
         nz, ny, nx = (int(v) for v in shape)

@@ -173,6 +173,31 @@ def test_adamw_first_step_identity():
             assert np.abs(x1 - want).max() < 1e-6 * (np.abs(x0).max() + lr)
 
 
+def test_save_and_load_round_trip(tmp_path):
+    """Parameters written by Model.save come back bit for bit in another
+    model, whose forward pass then equals the first model's."""
+    rng = np.random.default_rng(15)
+    kappa, S, E = _fields(rng, 1, (8, 8, 8))
+    a, b = vet.Model(), vet.Model()
+    a.set_params(_params(15))
+    a.save(tmp_path / "net.npz")
+    b.load(tmp_path / "net.npz")
+    for (Wa, ba), (Wb, bb) in zip(a.params(), b.params()):
+        np.testing.assert_array_equal(Wa, Wb)
+        np.testing.assert_array_equal(ba, bb)
+    outs = []
+    for m in (a, b):
+        m.features((8, 8, 8), 4, 0.125, _dev(kappa), _dev(S), _dev(E))
+        o = torch.empty(7 * 512, dtype=torch.float32, device="cuda")
+        m.forward(o)
+        torch.cuda.synchronize()
+        outs.append(o.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.savez(tmp_path / "other.npz", channels=np.int32(16))
+    with pytest.raises(ValueError):
+        b.load(tmp_path / "other.npz")
+
+
 def test_indicator_closed_form_with_bias_only_network():
     """A network whose weights are zero outputs its last bias everywhere:
     f = head(b) and r = max(-lambda_min, lambda_max - 1, exp(b6)) are then
