@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "G cell·angle updates/s and VET closures/s at fixed |Δf|≤1e-6 (plain) / ≤1e-2 (learned)"
 UNIT = "G cell·angle updates/s"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-MUFU_PER_CLK_PER_SM = 16    # ex2 results per clock per SM
+MUFU_PER_CLK_PER_SM = 32    # ex2 results per clock per SM on GB300 (csrc/peaks.cu measures 31.99)
 N_SM = 152
 
 
@@ -414,10 +414,17 @@ def run_ours(args, rank, world, local_rank):
     peak = MUFU_PER_CLK_PER_SM * N_SM * sm_max * 1e6 / 1e9  # G exp/s
     achieved = cell_segs / (cell_ms * 1e-3) / 1e9
     traffic = measured_traffic()
+    try:  # the unit count behind the peak, measured on this GPU
+        from paper_2202_08778_gb300 import peaks as _peaks
+
+        units = _peaks.measure()
+    except Exception as exc:  # noqa: BLE001 - reported, not fatal
+        units = {"error": str(exc)[:200]}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G exp/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "cell_pair_kernel<2,16> (FP32 cell pass on mirrored ray pairs)",
                 "peak_basis": f"MUFU ex2: {MUFU_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {sm_max:.0f} MHz",
-                "algorithmic": f"{cell_segs} cell-ray segments (one exp each) per launch"}
+                "algorithmic": f"{cell_segs} cell-ray segments (one exp each) per launch",
+                "measured_units_per_clk_per_sm": units}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -71,5 +71,23 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     return LIB
 
 
+PEAKS = os.path.join(OUT_DIR, "vet_peaks")
+
+
+def build_peaks(force: bool = False) -> str:
+    """Compile the unit-rate microbenchmark (csrc/peaks.cu) into an
+    executable next to libvet."""
+    src = os.path.join(CSRC, "peaks.cu")
+    if not force and os.path.exists(PEAKS) and os.path.getmtime(PEAKS) >= os.path.getmtime(src):
+        return PEAKS
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PEAKS + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", tmp], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on peaks.cu:\n{r.stderr}")
+    os.replace(tmp, PEAKS)
+    return PEAKS
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))

@@ -39,8 +39,10 @@ def test_lognormal128_every_cell_matches_oracle(ora):
     ctx.sync()
     f_ref, M_ref, _, _ = ora.vet_closure(k.astype(np.float64), s.astype(np.float64), ctx.directions(), p["B"], p["h"])
     eE, eFP = moment_errors(M.cpu().numpy(), M_ref)
+    ef = f_error(f.cpu().numpy(), f_ref, M_ref)
+    print(f"lognormal128 every cell: E rel {eE:.2e}, F/P rel {eFP:.2e}, max |df| {ef:.2e}")
     assert eE < RTOL32 and eFP < RTOL32, (eE, eFP)
-    assert f_error(f.cpu().numpy(), f_ref, M_ref) < FTOL32
+    assert ef < FTOL32
 
 
 def test_cloud_sampled_directions_and_shadow(ora):
