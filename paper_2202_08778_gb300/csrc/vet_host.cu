@@ -237,6 +237,18 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of pinned, mapped host memory (page-locked by
+// cudaHostAlloc or cudaHostRegister; under unified addressing such memory is
+// mapped), or nullptr for device or pageable memory.
+void *mapped_host_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Device views of the caller's arguments; host arguments are staged.
 struct Staging {
   vet_ctx *c;
@@ -268,23 +280,32 @@ vet_status check_ctx(vet_ctx *c, bool want_fp64) {
 }
 
 // Prepares device pointers for a call.  ins: inputs (ptr, elements, may be
-// null); outs: outputs.  Host pointers are copied to / from the staging
-// buffer on `st`.
+// null); outs: outputs.  Host inputs are copied to the staging buffer on
+// `st`.  Host outputs in pinned (mapped) memory are written by the kernels
+// directly, through their device address: the results cross the host link
+// as the kernels write them (each output element is written once), with no
+// separate copy afterwards; pageable host outputs are staged and copied
+// back.
 template <typename R>
 vet_status stage_args(vet_ctx *c, cudaStream_t st, std::vector<std::pair<const R *, size_t>> ins,
                       std::vector<std::pair<R *, size_t>> outs, std::vector<const R *> &din,
                       std::vector<R *> &dout, std::vector<std::pair<R *, R *>> &copy_back,
-                      std::vector<size_t> &copy_bytes) {
+                      std::vector<size_t> &copy_bytes, bool &any_host) {
   size_t need = 0;
   std::vector<bool> in_host(ins.size()), out_host(outs.size());
   for (size_t i = 0; i < ins.size(); ++i) {
     in_host[i] = ins[i].first && !is_device_ptr(ins[i].first);
     if (in_host[i]) need += round256(ins[i].second * sizeof(R));
   }
+  std::vector<void *> out_mapped(outs.size(), nullptr);
   for (size_t i = 0; i < outs.size(); ++i) {
     out_host[i] = outs[i].first && !is_device_ptr(outs[i].first);
-    if (out_host[i]) need += round256(outs[i].second * sizeof(R));
+    if (out_host[i]) out_mapped[i] = mapped_host_ptr(outs[i].first);
+    if (out_host[i] && !out_mapped[i]) need += round256(outs[i].second * sizeof(R));
   }
+  any_host = false;  // then the call returns only once its results are in place
+  for (bool h : in_host) any_host = any_host || h;
+  for (bool h : out_host) any_host = any_host || h;
   if (need) {
     vet_status s = reserve_stage(c, need);
     if (s != VET_OK) return s;
@@ -307,6 +328,10 @@ vet_status stage_args(vet_ctx *c, cudaStream_t st, std::vector<std::pair<const R
   for (size_t i = 0; i < outs.size(); ++i) {
     if (!out_host[i]) {
       dout.push_back(outs[i].first);
+      continue;
+    }
+    if (out_mapped[i]) {  // written in place; the call still synchronises
+      dout.push_back((R *)out_mapped[i]);
       continue;
     }
     R *d = (R *)(base + off);
@@ -381,10 +406,10 @@ vet_status do_trace(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *I_ou
   std::vector<R *> dout;
   std::vector<std::pair<R *, R *>> back;
   std::vector<size_t> bytes;
+  bool had_host = false;
   s = stage_args<R>(c, st, {{kappa, nc}, {S, nc}, {Ib, Ib ? (size_t)6 * c->N : 0}}, {{I_out, (size_t)c->N * nc}},
-                    din, dout, back, bytes);
+                    din, dout, back, bytes, had_host);
   if (s) return s;
-  const bool had_host = !back.empty() || din[0] != kappa || din[1] != S || din[2] != Ib;
   c->timed = false;
   if ((s = mark(c, 0, st))) return s;
   if ((s = run_face_pass<R>(c, din[0], din[1], din[2], st))) return s;
@@ -411,9 +436,9 @@ vet_status do_moments(vet_ctx *c, const R *I, R *M_out, void *stream, bool fp64)
   std::vector<R *> dout;
   std::vector<std::pair<R *, R *>> back;
   std::vector<size_t> bytes;
-  s = stage_args<R>(c, st, {{I, (size_t)c->N * nc}}, {{M_out, 10 * nc}}, din, dout, back, bytes);
+  bool had_host = false;
+  s = stage_args<R>(c, st, {{I, (size_t)c->N * nc}}, {{M_out, 10 * nc}}, din, dout, back, bytes, had_host);
   if (s) return s;
-  const bool had_host = !back.empty() || din[0] != I;
   cudaError_t e = vet::launch_moments<R>(c->dims.ncell, c->N, din[0], (const R *)c->d_coef, dout[0], st);
   if (e) return cuda_err(c, e, "moments launch");
   c->last_stream = st;
@@ -434,10 +459,10 @@ vet_status do_closure(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *f_
   std::vector<R *> dout;
   std::vector<std::pair<R *, R *>> back;
   std::vector<size_t> bytes;
+  bool had_host = false;
   s = stage_args<R>(c, st, {{kappa, nc}, {S, nc}, {Ib, Ib ? (size_t)6 * c->N : 0}},
-                    {{f_out, 6 * nc}, {M_out, M_out ? 10 * nc : 0}}, din, dout, back, bytes);
+                    {{f_out, 6 * nc}, {M_out, M_out ? 10 * nc : 0}}, din, dout, back, bytes, had_host);
   if (s) return s;
-  const bool had_host = !back.empty() || din[0] != kappa || din[1] != S || din[2] != Ib;
   c->timed = false;
   if ((s = mark(c, 0, st))) return s;
   cudaError_t e = cudaMemsetAsync(c->d_emax, 0, 8, st);

@@ -193,6 +193,25 @@ def test_host_buffers_give_identical_results():
     np.testing.assert_array_equal(M_host.reshape(10, -1), M_dev)
 
 
+def test_pinned_host_outputs_are_written_in_place():
+    """Outputs in pinned host memory are written by the kernels directly; the
+    call returns only once they are complete, with device inputs too."""
+    p = synth.blob_problem(n=32, B=8, nside=2, seed=1)
+    ctx = _ctx(p, vet.VET_FP32)
+    dev_in, _ = _inputs(p, np.float32)
+    f_dev, M_dev = _gpu_closure(ctx, dev_in, 32 ** 3, np.float32)
+    for inputs in ((dev_in[0], dev_in[1]), (dev_in[0].cpu().pin_memory(), dev_in[1].cpu().pin_memory())):
+        f_pin = torch.full((6 * 32 ** 3,), np.nan, dtype=torch.float32).pin_memory()
+        M_pin = torch.full((10 * 32 ** 3,), np.nan, dtype=torch.float32).pin_memory()
+        ctx.closure(inputs[0], inputs[1], None, f_pin, M_pin)
+        np.testing.assert_array_equal(f_pin.numpy().reshape(6, -1), f_dev)
+        np.testing.assert_array_equal(M_pin.numpy().reshape(10, -1), M_dev)
+    I_dev = _gpu_trace(ctx, dev_in, 32 ** 3, np.float32)
+    I_pin = torch.full((ctx.N * 32 ** 3,), np.nan, dtype=torch.float32).pin_memory()
+    ctx.trace(dev_in[0], dev_in[1], None, I_pin)
+    np.testing.assert_array_equal(I_pin.numpy().reshape(ctx.N, -1), I_dev)
+
+
 def test_repeat_runs_are_bit_identical():
     p = synth.lognormal_problem(n=32, B=16, nside=2, seed=41)
     ctx = _ctx(p, vet.VET_FP32)
