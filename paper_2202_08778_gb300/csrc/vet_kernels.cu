@@ -369,11 +369,15 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
   unsigned char *slots = smem + align16(sizeof(vec2_t<R>) * (size_t)ts.elems);
   const int bx = it.block % g.nbx, by = (it.block / g.nbx) % g.nby, bz = it.block / (g.nbx * g.nby);
   const int nblk = g.nbx * g.nby * g.nbz;
-  if (threadIdx.x == 0) {
-    mbar_init(&full, 1);
-    mbar_fence_init();
-    mbar_expect_tx(&full, (uint32_t)(sb * it.dir_count));
-    for (int j = 0; j < it.dir_count; ++j)
+  if (threadIdx.x < 32) {  // warp 0: one lane per staged direction
+    if (threadIdx.x == 0) {
+      mbar_init(&full, 1);
+      mbar_fence_init();
+      mbar_expect_tx(&full, (uint32_t)(sb * it.dir_count));
+    }
+    __syncwarp();
+    const int j = threadIdx.x;
+    if (j < it.dir_count)
       issue_slot<R>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full, TL.node_bytes);
   }
   load_tile<R, BC, kFaceThreads>(tile, ts, g, bx, by, bz, kappa, S);
@@ -1017,16 +1021,20 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
   const int mblock = (mz * g.nby + my) * g.nbx + mx;
   const int nblk = g.nbx * g.nby * g.nbz;
   const int cnt = it.dir_count;
-  if (threadIdx.x == 0) {
-    mbar_init(&full, 1);
-    mbar_fence_init();
-    mbar_expect_tx(&full, (uint32_t)((sb + fb3) * cnt));
-    for (int j = 0; j < cnt; ++j) {
+  if (threadIdx.x < 32) {  // warp 0: one lane per staged slot
+    if (threadIdx.x == 0) {
+      mbar_init(&full, 1);
+      mbar_fence_init();
+      mbar_expect_tx(&full, (uint32_t)((sb + fb3) * cnt));
+    }
+    __syncwarp();
+    const int j = threadIdx.x;
+    if (j < cnt)
       issue_slot<float>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full,
                         TL.node_bytes);
-      issue_slot<float>(slots + sb * cnt + fb3 * j, g, TL, mx, my, mz, it.mirror_begin + j, tpl_g, faces, bnd,
-                        &full, 0);
-    }
+    else if (j < 2 * cnt)
+      issue_slot<float>(slots + sb * cnt + fb3 * (j - cnt), g, TL, mx, my, mz, it.mirror_begin + (j - cnt), tpl_g,
+                        faces, bnd, &full, 0);
   }
   load_tile_mirrored<BC, kFaceThreads>(tile, ts, g, bx, by, bz, mx, my, mz, kappa, S);
   __syncthreads();
