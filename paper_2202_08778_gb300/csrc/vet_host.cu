@@ -219,6 +219,14 @@ vet_status build_context(vet_ctx *c) {
     return cuda_err(c, e, "upload templates");
   vet_status st = build_schedule(c, c->face_group);
   if (st != VET_OK) return st;
+  // the cell passes stage by this order: each entry also carries the
+  // direction's signs (bits 16-18, flag bit 19)
+  for (int k = 0; k < N; ++k) {
+    const auto *hd = reinterpret_cast<const vet::TplHead<R> *>(tpl.data() + (size_t)cell_order[k] * tbytes);
+    int bits = 0;
+    for (int a = 0; a < 3; ++a) bits |= (hd->sgn[a] < 0 ? 1 : 0) << a;
+    cell_order[k] |= (1 << 19) | (bits << 16);
+  }
   if ((e = cudaMalloc((void **)&c->d_cell_order, sizeof(int) * N))) return cuda_err(c, e, "cudaMalloc(order)");
   if ((e = cudaMemcpy(c->d_cell_order, cell_order.data(), sizeof(int) * N, cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload order");

@@ -230,7 +230,7 @@ template <typename R>
 __device__ __forceinline__ void issue_slot(unsigned char *slot, const GridDims &g, const TplLayout &TL, int bx,
                                            int by, int bz, int d, const unsigned char *__restrict__ tpl_g,
                                            const R *__restrict__ faces, const R *__restrict__ bnd, uint64_t *bar,
-                                           int tpl_bytes) {
+                                           int tpl_bytes, int sgn_bits = -1) {
   const unsigned char *src = tpl_g + (size_t)d * TL.bytes;
   if (tpl_bytes > 0) bulk_g2s(slot, src, (uint32_t)tpl_bytes, bar);
   const TplHead<R> *hd = reinterpret_cast<const TplHead<R> *>(src);
@@ -239,7 +239,7 @@ __device__ __forceinline__ void issue_slot(unsigned char *slot, const GridDims &
   const int b3[3] = {bx, by, bz};
   const int nb3[3] = {g.nbx, g.nby, g.nbz};
   for (int a = 0; a < 3; ++a) {
-    const int s = hd->sgn[a];
+    const int s = sgn_bits >= 0 ? ((sgn_bits >> a) & 1 ? -1 : 1) : hd->sgn[a];
     int nb[3] = {b3[0], b3[1], b3[2]};
     nb[a] -= s;
     const R *fsrc;
@@ -253,6 +253,12 @@ __device__ __forceinline__ void issue_slot(unsigned char *slot, const GridDims &
     bulk_g2s(slot + tpl_bytes + a * fb, fsrc, fb, bar);
   }
 }
+
+// Cell-pass order entries: the internal direction index, optionally with the
+// direction's signs (bit 16 + a set: component a negative; bit 19: signs
+// present), so that staging needs no read of the template head.
+__device__ __forceinline__ int order_dir(int v) { return v & 0xffff; }
+__device__ __forceinline__ int order_sgn(int v) { return (v >> 19) & 1 ? (v >> 16) & 7 : -1; }
 
 // Bytes of the three staged incoming faces of one direction.
 template <typename R>
@@ -495,7 +501,8 @@ __global__ void __launch_bounds__(kCellThreads, 2)
     unsigned char *buf = buf0 + (size_t)b * dt * sb;
     mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
     for (int j = 0; j < nd; ++j)
-      issue_slot<R>(buf + sb * j, g, TL, bx, by, bz, order[d0 + j], tpl_g, faces, bnd, &full[b], TL.bytes);
+      issue_slot<R>(buf + sb * j, g, TL, bx, by, bz, order_dir(order[d0 + j]), tpl_g, faces, bnd, &full[b], TL.bytes,
+                    order_sgn(order[d0 + j]));
   };
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -778,7 +785,11 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     unsigned char *buf = buf0 + (size_t)b * dt * sb;
     mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
     for (int j = 0; j < nd; ++j)
-      issue_slot<float>(buf + sb * j, g, TL, bx, by, bz, order[d0 + j], tpl_g, faces, bnd, &full[b], TL.bytes);
+    {
+      const int v = order[d0 + j];
+      issue_slot<float>(buf + sb * j, g, TL, bx, by, bz, order_dir(v), tpl_g, faces, bnd, &full[b], TL.bytes,
+                        order_sgn(v));
+    }
   };
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
