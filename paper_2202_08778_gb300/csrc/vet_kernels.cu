@@ -354,7 +354,7 @@ inline int pair_dir_tile(int B, int want) {
   int dt = want > 0 ? want : kDirTile;
   dt = (dt + 1) & ~1;
   if (dt > kMaxTune) dt = kMaxTune;
-  while (dt > 2 && pair_smem_bytes(B, 2 * dt) > kSmemMax) dt -= 2;
+  while (dt > 2 && pair_smem_bytes(B, 2 * dt) > kSmemMax - 4096) dt -= 2;  // 4 KB: the staged order
   return dt;
 }
 
@@ -767,6 +767,9 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
   constexpr int B = BC, B2 = B * B;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[2], empty[2];
+  constexpr int kOrdMax = 1024;  // direction sets up to nside = 8 keep their order in shared memory
+  __shared__ int s_ord[kOrdMax];
+  const bool ord_smem = g.ndir <= kOrdMax;
   const TileShape ts = cell_tile(B);
   const TplLayout TL = tpl_layout<float>(B);
   const int fstride = g.fstride;
@@ -784,9 +787,8 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     const int b = t & 1, d0 = t * dt, nd = min(dt, g.ndir - d0);
     unsigned char *buf = buf0 + (size_t)b * dt * sb;
     mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
-    for (int j = 0; j < nd; ++j)
-    {
-      const int v = order[d0 + j];
+    for (int j = 0; j < nd; ++j) {
+      const int v = (ord_smem && t >= 2) ? s_ord[d0 + j] : order[d0 + j];
       issue_slot<float>(buf + sb * j, g, TL, bx, by, bz, order_dir(v), tpl_g, faces, bnd, &full[b], TL.bytes,
                         order_sgn(v));
     }
@@ -800,6 +802,8 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     issue_tile(0);
     if (ntiles > 1) issue_tile(1);
   }
+  if (ord_smem)
+    for (int i = threadIdx.x; i < g.ndir; i += blockDim.x) s_ord[i] = order[i];
   load_tile_pair<BC>(tile, ts, g, bx, by, bz, kappa, S);
   __syncthreads();
 
@@ -1290,8 +1294,11 @@ cudaError_t set_smem_attrs() {
                         (const void *)cell_pair_kernel<1, 8>,  (const void *)cell_pair_kernel<1, 16>,
                         (const void *)cell_pair_kernel<2, 8>,  (const void *)cell_pair_kernel<2, 16>,
                         (const void *)face_pair_kernel<8>,     (const void *)face_pair_kernel<16>};
-  for (const void *f : pfns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  for (const void *f : pfns) {  // less their static shared memory
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
