@@ -378,7 +378,7 @@ inline bool mirror_templates(const unsigned char *ta, const unsigned char *tb, i
 inline long long build_schedule(const int nb[3], const int ob[9], int group, FaceItem *items, long long cap,
                                 int *level_off, const int *level_group = nullptr, bool paired = false) {
   const int nlevels = nb[0] + nb[1] + nb[2] - 2;
-  // visit(L, f) calls f(block, d0, count) for every item of level L
+  // visit(L, f) calls f(block, d0, count, mirror d0, octant) for every item of level L
   auto visit = [&](int L, auto &&f) {
     for (int o = 0; o < 8; o += paired ? 2 : 1) {
       if (ob[o + 1] == ob[o]) continue;
@@ -398,21 +398,21 @@ inline long long build_schedule(const int nb[3], const int ob[9], int group, Fac
             if (lv != L || live == 0) continue;
             const int id = (bz * nb[1] + by) * nb[0] + bx;
             const int g = level_group ? level_group[L] : group;
-            for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += g) f(id, d0, std::min(g, ob[o + 1] - d0), d0 + mshift);
+            for (int d0 = ob[o]; d0 < ob[o + 1]; d0 += g) f(id, d0, std::min(g, ob[o + 1] - d0), d0 + mshift, o);
           }
     }
   };
   long long total = 0;
   for (int L = 0; L < nlevels; ++L) {
     level_off[L] = (int)total;
-    visit(L, [&](int, int, int, int) { ++total; });
+    visit(L, [&](int, int, int, int, int) { ++total; });
   }
   level_off[nlevels] = (int)total;
   if (total > cap) return -1;
   if (!items) return total;
   long long k = 0;
   for (int L = 0; L < nlevels; ++L)
-    visit(L, [&](int id, int d0, int cnt, int m0) { items[k++] = {id, d0, cnt, paired ? m0 : 0}; });
+    visit(L, [&](int id, int d0, int cnt, int m0, int o) { items[k++] = {id, d0, cnt, paired ? m0 : 0, o}; });
   return k;
 }
 

@@ -138,6 +138,7 @@ struct FaceItem {
   int dir_begin;     // internal direction index
   int dir_count;
   int mirror_begin;  // paired face pass: internal index of the antipode of dir_begin
+  int octant;        // the directions' octant: bit a set where component a is negative
 };
 
 // Launchers (vet_kernels.cu).  All return the cudaGetLastError() of the

@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
     __syncwarp();
     const int j = threadIdx.x;
     if (j < it.dir_count)
-      issue_slot<R>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full, TL.node_bytes);
+      issue_slot<R>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full, TL.node_bytes,
+                    it.octant);
   }
   load_tile<R, BC, kFaceThreads>(tile, ts, g, bx, by, bz, kappa, S);
   __syncthreads();
@@ -1044,12 +1045,12 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     }
     __syncwarp();
     const int j = threadIdx.x;
-    if (j < cnt)
+    if (j < cnt)  // the octant's signs: no read of the template head before the copies
       issue_slot<float>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full,
-                        TL.node_bytes);
-    else if (j < 2 * cnt)
+                        TL.node_bytes, it.octant);
+    else if (j < 2 * cnt)  // antipodes: the opposite octant
       issue_slot<float>(slots + sb * cnt + fb3 * (j - cnt), g, TL, mx, my, mz, it.mirror_begin + (j - cnt), tpl_g,
-                        faces, bnd, &full, 0);
+                        faces, bnd, &full, 0, 7 - it.octant);
   }
   load_tile_mirrored<BC, kFaceThreads>(tile, ts, g, bx, by, bz, mx, my, mz, kappa, S);
   __syncthreads();

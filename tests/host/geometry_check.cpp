@@ -80,7 +80,11 @@ int main(int argc, char **argv) {
     for (int L = 0; L < nl; ++L) {
       std::multiset<std::tuple<int, int>> a, b;
       for (int i = off[L]; i < off[L + 1]; ++i)
-        for (int j = 0; j < U[i].dir_count; ++j) a.insert({U[i].block, U[i].dir_begin + j});
+        for (int j = 0; j < U[i].dir_count; ++j) {
+          a.insert({U[i].block, U[i].dir_begin + j});
+          if (vet::geom::octant_of(&d[4 * order[U[i].dir_begin + j]]) != U[i].octant)
+            return fail("item octant differs from its directions'");
+        }
       for (int i = poff[L]; i < poff[L + 1]; ++i) {
         const int bx = P[i].block % nb[0], by = (P[i].block / nb[0]) % nb[1], bz = P[i].block / (nb[0] * nb[1]);
         const int mb = ((nb[2] - 1 - bz) * nb[1] + (nb[1] - 1 - by)) * nb[0] + (nb[0] - 1 - bx);
@@ -89,6 +93,8 @@ int main(int argc, char **argv) {
           b.insert({P[i].block, P[i].dir_begin + j});
           b.insert({mb, P[i].mirror_begin + j});
           const double *x = &d[4 * order[P[i].dir_begin + j]], *y = &d[4 * order[P[i].mirror_begin + j]];
+          if (vet::geom::octant_of(x) != P[i].octant || vet::geom::octant_of(y) != 7 - P[i].octant)
+            return fail("paired item octant differs from its directions'");
           if (std::fabs(x[0] + y[0]) + std::fabs(x[1] + y[1]) + std::fabs(x[2] + y[2]) > 1e-12)
             return fail("paired item's mirror directions are not antipodes");
         }
