@@ -260,6 +260,15 @@ __device__ __forceinline__ void issue_slot(unsigned char *slot, const GridDims &
 __device__ __forceinline__ int order_dir(int v) { return v & 0xffff; }
 __device__ __forceinline__ int order_sgn(int v) { return (v >> 19) & 1 ? (v >> 16) & 7 : -1; }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream drains; it
+// runs its independent prologue, then griddep_wait() blocks the calling
+// thread until the predecessor has completed and its writes are visible
+// (a no-op for an ordinary launch).  griddep_launch_dependents() lets the
+// successor start once every CTA of this grid has called it or exited.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 // Bytes of the three staged incoming faces of one direction.
 template <typename R>
 __host__ __device__ inline size_t faces_bytes(int B) {
@@ -800,6 +809,7 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     mbar_init(&empty[0], nwarps);
     mbar_init(&empty[1], nwarps);
     mbar_fence_init();
+    griddep_wait();  // the faces are the face pass's output
     issue_tile(0);
     if (ntiles > 1) issue_tile(1);
   }
@@ -1037,7 +1047,11 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
   const int mblock = (mz * g.nby + my) * g.nbx + mx;
   const int nblk = g.nbx * g.nby * g.nbz;
   const int cnt = it.dir_count;
+  griddep_launch_dependents();  // the next level may start its prologue
+  // kappa and S are the call's inputs: loaded before the previous level ends
+  load_tile_mirrored<BC, kFaceThreads>(tile, ts, g, bx, by, bz, mx, my, mz, kappa, S);
   if (threadIdx.x < 32) {  // warp 0: one lane per staged slot
+    griddep_wait();        // the incoming faces are the previous level's output
     if (threadIdx.x == 0) {
       mbar_init(&full, 1);
       mbar_fence_init();
@@ -1052,7 +1066,6 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
       issue_slot<float>(slots + sb * cnt + fb3 * (j - cnt), g, TL, mx, my, mz, it.mirror_begin + (j - cnt), tpl_g,
                         faces, bnd, &full, 0, 7 - it.octant);
   }
-  load_tile_mirrored<BC, kFaceThreads>(tile, ts, g, bx, by, bz, mx, my, mz, kappa, S);
   __syncthreads();
   if (!mbar_wait_warp(&full, 0, spin_limit, status, 1)) {
     if (threadIdx.x == 0) mbar_wait(&full, 0, kDrainPolls, status, 8);
@@ -1243,8 +1256,17 @@ void face_launch(const GridDims &g, const R *kappa, const R *S, const unsigned c
                  int nitems, int max_dirs, R *faces, const R *bnd, long long spin, int *status, cudaStream_t st) {
   if constexpr (sizeof(R) == sizeof(float) && BC != 0) {
     if (g.face_paired) {
-      face_pair_kernel<BC><<<nitems, kFaceThreads, face_pair_smem_bytes(BC, max_dirs), st>>>(
-          g, kappa, S, tpl, items, faces, bnd, spin, status);
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.gridDim = dim3(nitems);
+      cfg.blockDim = dim3(kFaceThreads);
+      cfg.dynamicSmemBytes = face_pair_smem_bytes(BC, max_dirs);
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, face_pair_kernel<BC>, g, kappa, S, tpl, items, faces, bnd, spin, status);
       return;
     }
   }
@@ -1273,9 +1295,18 @@ void pair_launch(const GridDims &g, const float *kappa, const float *S, const un
   const int parts = BC * BC * BC / 2 / pair_threads(BC);
   const int nblk = block_list ? nlist : g.nbx * g.nby * g.nbz;
   const int dt = pair_dir_tile(BC, g.dir_tile);
-  cell_pair_kernel<MODE, BC><<<nblk * parts, pair_threads(BC), pair_smem_bytes(BC, 2 * dt), st>>>(
-      g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out, E_out, f_out, emax_bits, spin, status,
-      block_list);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // prologue overlaps the face pass's end
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3(nblk * parts);
+  cfg.blockDim = dim3(pair_threads(BC));
+  cfg.dynamicSmemBytes = pair_smem_bytes(BC, 2 * dt);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, cell_pair_kernel<MODE, BC>, g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out,
+                     E_out, f_out, emax_bits, spin, status, block_list);
 }
 
 template <typename R>
