@@ -384,7 +384,10 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
   unsigned char *slots = smem + align16(sizeof(vec2_t<R>) * (size_t)ts.elems);
   const int bx = it.block % g.nbx, by = (it.block / g.nbx) % g.nby, bz = it.block / (g.nbx * g.nby);
   const int nblk = g.nbx * g.nby * g.nbz;
+  griddep_launch_dependents();  // as in face_pair_kernel
+  load_tile<R, BC, kFaceThreads>(tile, ts, g, bx, by, bz, kappa, S);
   if (threadIdx.x < 32) {  // warp 0: one lane per staged direction
+    griddep_wait();        // the incoming faces are the previous level's output
     if (threadIdx.x == 0) {
       mbar_init(&full, 1);
       mbar_fence_init();
@@ -396,7 +399,6 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
       issue_slot<R>(slots + sb * j, g, TL, bx, by, bz, it.dir_begin + j, tpl_g, faces, bnd, &full, TL.node_bytes,
                     it.octant);
   }
-  load_tile<R, BC, kFaceThreads>(tile, ts, g, bx, by, bz, kappa, S);
   __syncthreads();
   if (!mbar_wait_warp(&full, 0, spin_limit, status, 1)) {
     // the copies this CTA issued must land before its shared memory is
@@ -1270,8 +1272,17 @@ void face_launch(const GridDims &g, const R *kappa, const R *S, const unsigned c
       return;
     }
   }
-  face_pass_kernel<R, BC><<<nitems, kFaceThreads, face_smem_bytes<R>(g.B, max_dirs), st>>>(g, kappa, S, tpl, items,
-                                                                                           faces, bnd, spin, status);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3(nitems);
+  cfg.blockDim = dim3(kFaceThreads);
+  cfg.dynamicSmemBytes = face_smem_bytes<R>(g.B, max_dirs);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, face_pass_kernel<R, BC>, g, kappa, S, tpl, items, faces, bnd, spin, status);
 }
 
 template <typename R, int MODE, int BC>
