@@ -352,11 +352,6 @@ int cell_dir_tile(int B, int want) {
 // ---------------------------------------------------------------- face pass
 constexpr int kFaceThreads = 512;
 
-// Face pass: one CTA per item (a block and up to kFaceGroup directions of one
-// octant at the same wavefront level).  One thread issues the TMA bulk copies
-// of the item's templates and incoming faces, all in flight at once, while
-// the CTA loads the block's kappa/S tile; then the (direction, node) rays are
-// spread over the threads.
 // Directions per tile of the paired cell pass: an even number (whole pairs)
 // whose two buffers fit, at most the tuned tile rounded up to even.
 inline int pair_dir_tile(int B, int want) {
@@ -367,6 +362,13 @@ inline int pair_dir_tile(int B, int want) {
   return dt;
 }
 
+// Face pass: one CTA per item (a block and up to kFaceGroup directions of one
+// octant at the same wavefront level).  The CTA loads the block's kappa/S
+// tile; the lanes of warp 0 then issue the TMA bulk copies of the item's
+// template parts and incoming faces, one slot each, all in flight at once
+// (once the previous level has completed: each level is a programmatic
+// dependent launch of the one before); then the (direction, node) rays are
+// spread over the threads.
 template <typename R, int BC>
 __global__ void __launch_bounds__(kFaceThreads, 3)
     face_pass_kernel(GridDims g, const R *__restrict__ kappa, const R *__restrict__ S,
