@@ -235,6 +235,42 @@ def batch_measurement(local_rank, reps: int = 20):
             "speedup_vs_sequential": t_seq / t_batch}
 
 
+def local_closure_measurement(ctx, kappa, S, flush, reps: int = 20):
+    """The M1 local closure (paper Sec. 6.1; vet_local_closure) on the
+    moments of this workload, against the HBM copy bandwidth: 16 bytes read
+    and 24 written per cell, L2 flushed before every timed launch."""
+    import torch
+
+    from paper_2202_08778_gb300 import vet
+
+    n0 = kappa.numel()
+    M0 = torch.empty(10 * n0, dtype=torch.float32, device=kappa.device)
+    f = torch.empty(6 * n0, dtype=torch.float32, device=kappa.device)
+    ctx.closure(kappa, S, None, f, M0)
+    # the workload's moments repeated 8 times (16.8M cells, 671 MB moved per
+    # launch), so that the launch's ramp is small against its traffic
+    M = M0.view(10, n0).repeat(1, 8).reshape(-1)
+    n = 8 * n0
+    T = torch.empty(6 * n, dtype=torch.float32, device=kappa.device)
+    ms = []
+    for i in range(reps + 3):
+        flush.fill_(i & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        vet.local_closure(vet.VET_CLOSURE_M1, M, T, n)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    gbs = 40.0 * n / (t * 1e-3) / 1e9
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    return {"kernel": "m1_kernel (vet_local_closure, VET_CLOSURE_M1)", "cells": n,
+            "input": "the workload's moments (vet_closure) repeated 8 times", "ms": t,
+            "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "algorithmic": "40 bytes per cell (E, F read; 6 components written)"}
+
+
 def learned_measurement(local_rank):
     """The learned closure at 256^3 in 16^3 blocks with 192 directions (the
     lognormal generator, seed 3) against the plain closure on the same GPU.
@@ -417,6 +453,8 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": float(n) * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
            "d2h_bytes_per_step": 6 * n * 4, "ms_per_step": 1e3 * e2e_s}
 
+    local = local_closure_measurement(ctx, kappa, S, flush) if rank == 0 and world == 1 else None
+
     # roofline of the dominant kernel (the cell pass), from the live events
     cell_ms = statistics.median(ph[1] for ph in phase)
     face_ms = statistics.median(ph[0] for ph in phase)
@@ -446,6 +484,8 @@ def run_ours(args, rank, world, local_rank):
             "work": {"cell_segments": cell_segs, "face_segments": face_segs,
                      "segments_per_cell_angle": (cell_segs + face_segs) / (n * N)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps}
+    if local is not None:
+        line["local_closure_m1"] = local
     clocks = clk.summary()
     if clocks is not None:
         line["clocks"] = clocks

@@ -307,6 +307,25 @@ const char *vet_model_last_error(const vet_model *model);
 const char *vet_last_error(const vet_ctx *ctx);
 
 /* ------------------------------------------------------------------------
+ * Local closures (paper Sec. 6.1, the comparison with FLD and M1): the
+ * Eddington tensor of each cell from that cell's moments alone.
+ *   VET_CLOSURE_EDDINGTON: T = I / 3 (M may be NULL).
+ *   VET_CLOSURE_M1:        T = (1 - chi)/2 I + (3 chi - 1)/2 n n with
+ *                          n = F / |F| and the Levermore factor
+ *                          chi(f) = (3 + 4 f^2) / (5 + 2 sqrt(4 - 3 f^2)),
+ *                          f = |F| / E (c = 1).
+ * Readings: f is clipped to [0, 1]; F = 0 gives chi = 1/3 (T = I / 3); E <= 0
+ * gives T = I / 3.
+ * M: [10][ncell] moments in vet_moments' layout (only E, Fx, Fy, Fz are
+ * read); T_out: [6][ncell] (xx, yy, zz, xy, xz, yz).  Both device memory,
+ * caller-owned; work is enqueued on `stream` and the call returns before it
+ * runs.  VET_EINVAL for a bad kind, a negative ncell, a missing or host
+ * pointer; VET_ECUDA for a failed launch.  Needs no context.
+ * ---------------------------------------------------------------------- */
+enum { VET_CLOSURE_EDDINGTON = 0, VET_CLOSURE_M1 = 1 };
+vet_status vet_local_closure(int kind, long long ncell, const float *M, float *T_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * An entry point that allocates nothing (the paper has no counterpart; it
  * exists for callers of this library, not for the method).
  *

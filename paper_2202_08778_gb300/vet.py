@@ -33,6 +33,7 @@ EXPORTS = (
     "vet_model_create", "vet_model_destroy", "vet_model_num_params", "vet_model_set_params", "vet_model_get_params",
     "vet_model_get_grads", "vet_model_features", "vet_model_forward", "vet_model_backward", "vet_model_step",
     "vet_closure_learned", "vet_model_last_timing", "vet_model_last_indicator", "vet_model_last_error",
+    "vet_local_closure",
 )
 
 #: functions whose return value is not a vet_status
@@ -126,6 +127,7 @@ def load(build_if_missing: bool = True):
         lib.vet_model_last_indicator.argtypes = [vp, vp, vp]
         lib.vet_model_last_error.argtypes = [vp]
         lib.vet_model_last_error.restype = ctypes.c_char_p
+        lib.vet_local_closure.argtypes = [i, ctypes.c_longlong, vp, vp, vp]
         for name in EXPORTS:
             if name not in _NOT_STATUS:
                 getattr(lib, name).restype = ctypes.c_int
@@ -277,6 +279,23 @@ class Context:
                                            _ptr(Ib, np.float32, 6 * self.N, "Ib"), ctypes.byref(fg),
                                            ctypes.byref(dt), _stream(stream)))
         return fg.value, dt.value
+
+
+VET_CLOSURE_EDDINGTON, VET_CLOSURE_M1 = 0, 1
+
+
+def local_closure(kind: int, M, T_out, ncell: int | None = None, stream=None):
+    """vet_local_closure: the Eddington (T = I/3) or M1 tensor of every cell
+    from its moments M [10][ncell] into T_out [6][ncell] (device tensors;
+    M may be None for the Eddington closure)."""
+    lib = load()
+    if ncell is None:
+        ncell = T_out.numel() // 6
+    st = lib.vet_local_closure(int(kind), int(ncell), _ptr(M, np.float32, 10 * ncell, "M"),
+                               _ptr(T_out, np.float32, 6 * ncell, "T_out"), _stream(stream))
+    if st != VET_OK:
+        raise VetError(st, "vet_local_closure")
+    return T_out
 
 
 def closure_noalloc(shape, block: int, h: float, nside: int, kappa, S, Ib, f_out, M_out=None,
