@@ -265,10 +265,15 @@ def local_closure_measurement(ctx, kappa, S, flush, reps: int = 20):
     t = statistics.median(ms)
     gbs = 40.0 * n / (t * 1e-3) / 1e9
     peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    # how far the local closure is from the ray-traced one on this field
+    d = (T.view(6, n)[:, :n0] - f.view(6, n0)).abs().amax(dim=0)  # the first copy's cells
+    vs_vet = {"mean": float(d.mean()), "p99": float(d.quantile(0.99)) if n0 <= (1 << 24) else None,
+              "max": float(d.max())}
     return {"kernel": "m1_kernel (vet_local_closure, VET_CLOSURE_M1)", "cells": n,
             "input": "the workload's moments (vet_closure) repeated 8 times", "ms": t,
             "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-            "algorithmic": "40 bytes per cell (E, F read; 6 components written)"}
+            "algorithmic": "40 bytes per cell (E, F read; 6 components written)",
+            "max_abs_dT_vs_vet": vs_vet}
 
 
 def learned_measurement(local_rank):
