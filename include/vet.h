@@ -326,6 +326,27 @@ enum { VET_CLOSURE_EDDINGTON = 0, VET_CLOSURE_M1 = 1 };
 vet_status vet_local_closure(int kind, long long ncell, const float *M, float *T_out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Direct radiation of a point source (paper Sec. 2.2.6, "Point Sources
+ * Contribution"): the energy and momentum deposition rates of a source of
+ * luminosity L at xs in every cell of the grid, from the optical depth
+ * along the straight ray from the source through the cell centre:
+ *   Edot = L e^{-tau_*} (1 - e^{-tau_cell}) / (4 pi r^2 dr),  pdot = Edot r_hat
+ * with tau_* the optical depth from the source to where the ray enters the
+ * cell (0 in the source's own cell), dr the ray's length inside the cell,
+ * tau_cell = kappa dr, r the distance to the cell centre and c = 1; 1 -
+ * e^{-tau_cell} is evaluated as -expm1(-tau_cell) (the paper's small-tau
+ * Taylor form without a switch).  A cell whose centre is the source gets 0.
+ * grid: cells and h (block is ignored); xs: host, length units, inside the
+ * grid [0, n h) per axis; kappa: [nz][ny][nx] opacity to the direct
+ * radiation per unit length; Edot_out: [cells]; pdot_out: [3][cells] or
+ * NULL.  Field pointers are device memory; work is enqueued on `stream`.
+ * VET_EINVAL for a bad grid, a source outside it or a missing or host
+ * pointer; VET_ECUDA for a failed launch.  Needs no context.
+ * ---------------------------------------------------------------------- */
+vet_status vet_point_source(const vet_grid *grid, const double xs[3], double L, const float *kappa, float *Edot_out,
+                            float *pdot_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * An entry point that allocates nothing (the paper has no counterpart; it
  * exists for callers of this library, not for the method).
  *

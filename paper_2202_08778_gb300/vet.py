@@ -33,7 +33,7 @@ EXPORTS = (
     "vet_model_create", "vet_model_destroy", "vet_model_num_params", "vet_model_set_params", "vet_model_get_params",
     "vet_model_get_grads", "vet_model_features", "vet_model_forward", "vet_model_backward", "vet_model_step",
     "vet_closure_learned", "vet_model_last_timing", "vet_model_last_indicator", "vet_model_last_error",
-    "vet_local_closure",
+    "vet_local_closure", "vet_point_source",
 )
 
 #: functions whose return value is not a vet_status
@@ -128,6 +128,8 @@ def load(build_if_missing: bool = True):
         lib.vet_model_last_error.argtypes = [vp]
         lib.vet_model_last_error.restype = ctypes.c_char_p
         lib.vet_local_closure.argtypes = [i, ctypes.c_longlong, vp, vp, vp]
+        lib.vet_point_source.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                         vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in _NOT_STATUS:
                 getattr(lib, name).restype = ctypes.c_int
@@ -296,6 +298,24 @@ def local_closure(kind: int, M, T_out, ncell: int | None = None, stream=None):
     if st != VET_OK:
         raise VetError(st, "vet_local_closure")
     return T_out
+
+
+def point_source(shape, h: float, xs, L: float, kappa, Edot_out, pdot_out=None, stream=None):
+    """vet_point_source: energy (Edot_out [cells]) and momentum (pdot_out
+    [3][cells], optional) deposition rates of a point source of luminosity L
+    at xs (length units) in a grid of `shape` = (nz, ny, nx) cells of edge h;
+    kappa [nz][ny][nx] is the opacity to the direct radiation (device)."""
+    lib = load()
+    nz, ny, nx = shape
+    n = int(nz) * int(ny) * int(nx)
+    g = _Grid(int(nx), int(ny), int(nz), 1, float(h))
+    x = (ctypes.c_double * 3)(*[float(v) for v in xs])
+    st = lib.vet_point_source(ctypes.byref(g), x, float(L), _ptr(kappa, np.float32, n, "kappa"),
+                              _ptr(Edot_out, np.float32, n, "Edot_out"), _ptr(pdot_out, np.float32, 3 * n, "pdot_out"),
+                              _stream(stream))
+    if st != VET_OK:
+        raise VetError(st, "vet_point_source")
+    return Edot_out
 
 
 def closure_noalloc(shape, block: int, h: float, nside: int, kappa, S, Ib, f_out, M_out=None,
