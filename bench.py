@@ -276,6 +276,40 @@ def local_closure_measurement(ctx, kappa, S, flush, reps: int = 20):
             "max_abs_dT_vs_vet": vs_vet}
 
 
+def point_source_measurement(kappa, shape, h, flush, reps: int = 10):
+    """The point-source deposition (paper Sec. 2.2.6; vet_point_source) of
+    a source at the centre of this workload's grid, opacity = its kappa.
+    Work unit: a cell a ray crosses, counted as the planes between the
+    source and the cell centre plus one."""
+    import numpy as np
+    import torch
+
+    from paper_2202_08778_gb300 import vet
+
+    nz, ny, nx = shape
+    n = nz * ny * nx
+    xs = (0.5 * nx * h, 0.5 * ny * h, 0.5 * nz * h)
+    E = torch.empty(n, dtype=torch.float32, device=kappa.device)
+    p = torch.empty(3 * n, dtype=torch.float32, device=kappa.device)
+    ms = []
+    for r in range(reps + 3):
+        flush.fill_(r & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        vet.point_source(shape, h, xs, 1.0, kappa, E, p)
+        b.record()
+        torch.cuda.synchronize()
+        if r >= 3:
+            ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cross = float((np.abs(i - nx // 2 + (i < nx // 2)) + np.abs(j - ny // 2 + (j < ny // 2))
+                   + np.abs(k - nz // 2 + (k < nz // 2)) + 1).sum())
+    return {"kernel": "point_kernel (vet_point_source)", "workload": "source at the grid centre, kappa of the workload",
+            "cells": n, "ms": t, "cell_crossings": cross, "G_crossings_per_s": cross / (t * 1e-3) / 1e9,
+            "rate": n / (t * 1e-3) / 1e9, "rate_unit": "G cells/s"}
+
+
 def learned_measurement(local_rank):
     """The learned closure at 256^3 in 16^3 blocks with 192 directions (the
     lognormal generator, seed 3) against the plain closure on the same GPU.
@@ -459,6 +493,8 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": 6 * n * 4, "ms_per_step": 1e3 * e2e_s}
 
     local = local_closure_measurement(ctx, kappa, S, flush) if rank == 0 and world == 1 else None
+    point = (point_source_measurement(kappa, p["kappa"].shape, p["h"], flush)
+             if rank == 0 and world == 1 else None)
 
     # roofline of the dominant kernel (the cell pass), from the live events
     cell_ms = statistics.median(ph[1] for ph in phase)
@@ -491,6 +527,8 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps}
     if local is not None:
         line["local_closure_m1"] = local
+    if point is not None:
+        line["point_source"] = point
     clocks = clk.summary()
     if clocks is not None:
         line["clocks"] = clocks
