@@ -65,25 +65,30 @@ __global__ void __launch_bounds__(256) point_kernel(PointArgs a, const float *__
         t_out = fminf(t_out, fmaxf(t1, t2));
       }
     const float dr = t_out - t_in;
-    // walk from the source cell to the entry of the target cell
+    // walk from the source cell to the entry of the target cell: the next
+    // crossing of each axis is kept, and only the axis just crossed has its
+    // next crossing recomputed (from the source position, not accumulated)
     int cur[3] = {(int)floorf(a.xs[0]), (int)floorf(a.xs[1]), (int)floorf(a.xs[2])};
+    const long long sstride[3] = {1, a.nx, (long long)a.nx * a.ny};
+    float tm[3];
+    int stp[3];
+    long long sidx[3];
+    for (int q = 0; q < 3; ++q) {
+      stp[q] = d[q] > 0.f ? 1 : -1;
+      sidx[q] = d[q] > 0.f ? sstride[q] : -sstride[q];
+      tm[q] = d[q] != 0.f ? (cur[q] + (d[q] > 0.f ? 1 : 0) - a.xs[q]) * inv[q] : INFINITY;
+    }
+    long long idx = ((long long)cur[2] * a.ny + cur[1]) * a.nx + cur[0];
     float t = 0.f, tau = 0.f;
     for (int s = 0; s < cap && t < t_in - 1e-5f; ++s) {
-      float tn = INFINITY;
-      int ax = 0;
-      for (int q = 0; q < 3; ++q)
-        if (d[q] != 0.f) {
-          const float tp = (cur[q] + (d[q] > 0.f ? 1 : 0) - a.xs[q]) * inv[q];
-          if (tp < tn) {
-            tn = tp;
-            ax = q;
-          }
-        }
-      tn = fminf(tn, t_in);
-      if (cur[0] >= 0 && cur[0] < a.nx && cur[1] >= 0 && cur[1] < a.ny && cur[2] >= 0 && cur[2] < a.nz)
-        tau = fmaf(kappa[((long long)cur[2] * a.ny + cur[1]) * a.nx + cur[0]], tn - t, tau);
+      const int ax = tm[0] <= tm[1] ? (tm[0] <= tm[2] ? 0 : 2) : (tm[1] <= tm[2] ? 1 : 2);
+      const float tn = fminf(tm[ax], t_in);
+      if ((unsigned)cur[0] < (unsigned)a.nx && (unsigned)cur[1] < (unsigned)a.ny && (unsigned)cur[2] < (unsigned)a.nz)
+        tau = fmaf(kappa[idx], tn - t, tau);
       t = tn;
-      cur[ax] += d[ax] > 0.f ? 1 : -1;
+      cur[ax] += stp[ax];
+      idx += sidx[ax];
+      tm[ax] = (cur[ax] + (stp[ax] > 0 ? 1 : 0) - a.xs[ax]) * inv[ax];
     }
     const float taus = tau * a.h, drl = dr * a.h, rl = r * a.h;
     const float tc = kappa[c] * drl;
