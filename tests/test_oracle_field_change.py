@@ -1,8 +1,10 @@
 """Pins of the change-gate oracle (oracle/field_change.py; the reuse of f
-across time steps of paper Sec. 7): block numbering and maxima against
-brute-force loops over cells, exact values of single-cell perturbations of
-either sign, symmetry, non-finite inputs, scale invariance of the decision,
-and the decision table."""
+across time steps of paper Sec. 7): the opacity measure against the exact
+change of a cell's transmission (an upper bound everywhere, equal to the
+optical-depth change for thin cells, negligible for thick ones), block
+numbering and maxima against brute-force loops over cells, exact values of
+single-cell perturbations of either sign, symmetry, non-finite inputs, scale
+invariance of the decision, and the decision table."""
 import math
 
 import numpy as np
@@ -21,7 +23,9 @@ def _brute(kappa, S, kr, sr, h, B):
         for j in range(ny):
             for i in range(nx):
                 b = i // B + nbx * (j // B + nby * (k // B))
-                dt = float(np.float32(abs(np.float32(kappa[k, j, i]) - np.float32(kr[k, j, i]))) * np.float32(h))
+                a = np.float32(kappa[k, j, i]) * np.float32(h)
+                c = np.float32(kr[k, j, i]) * np.float32(h)
+                dt = abs(a - c) / ((1 + a / 2) * (1 + c / 2))
                 ds = float(abs(np.float32(S[k, j, i]) - np.float32(sr[k, j, i])))
                 out[b, 0] = max(out[b, 0], np.float32(dt))
                 out[b, 1] = max(out[b, 1], ds)
@@ -36,6 +40,31 @@ def _fields(shape, seed):
     kr = (k * rng.uniform(0.9, 1.1, shape)).astype(np.float32)
     sr = (s * rng.uniform(0.9, 1.1, shape)).astype(np.float32)
     return k, s, kr, sr
+
+
+def _per_cell(a, b, h):
+    """The opacity measure of optical depths a -> b, one 2^3 block each."""
+    n = a.size
+    k = np.repeat(np.float32(a / h), 2).reshape(1, 1, 2 * n).repeat(2, 0).repeat(2, 1)
+    kr = np.repeat(np.float32(b / h), 2).reshape(1, 1, 2 * n).repeat(2, 0).repeat(2, 1)
+    one = np.ones_like(k)
+    return fc.change(k, one, kr, one, h, 2)[3::3], np.float64(k[0, 0, ::2] * np.float32(h)), \
+        np.float64(kr[0, 0, ::2] * np.float32(h))
+
+
+def test_opacity_measure_bounds_the_change_of_transmission():
+    rng = np.random.default_rng(7)
+    a = np.exp(rng.uniform(-12, 5, 4096))                # optical depths 6e-6 .. 150
+    b = a * np.exp(rng.normal(0, 0.5, 4096))
+    got, aa, bb = _per_cell(a, b, 0.5)
+    exact = np.abs(np.exp(-aa) - np.exp(-bb))
+    assert np.all(got >= exact * (1 - 1e-5))               # an upper bound
+    thin = np.maximum(aa, bb) < 1e-3
+    assert thin.sum() > 100
+    np.testing.assert_allclose(got[thin], np.abs(aa - bb)[thin], rtol=2e-3)   # ~ |dtau| when thin
+    # thick cells: a large change of optical depth barely counts (50 -> 60: 10 / (26 * 31))
+    got, aa, bb = _per_cell(np.array([50.0]), np.array([60.0]), 0.5)
+    assert got[0] == np.float32(10.0) / np.float32(26.0 * 31.0)
 
 
 @pytest.mark.parametrize("shape,B", [((4, 6, 8), 2), ((6, 3, 9), 3), ((8, 8, 4), 4)])
@@ -55,18 +84,21 @@ def test_single_cell_perturbation_lands_in_its_block_only(delta):
     s = np.full(shape, 3.0, np.float32)
     kp, sp = k.copy(), s.copy()
     kp[5, 2, 7] += delta       # block (i 3, j 1, k 2) -> 3 + 4 * (1 + 2 * 2) = 23
+    # a = (1 + delta) / 4, b = 1/4: |a - b| / ((1 + a/2)(1 + b/2)) =
+    # (1/8) / ((19/16)(9/8)) = 16/171 for delta = 1/2, (1/8) / ((17/16)(9/8)) = 16/153 for -1/2
+    dtrans = np.float32(16 / 171) if delta > 0 else np.float32(16 / 153)
     sp[0, 3, 0] -= 2 * delta   # block (0, 1, 0) -> 4
     got = fc.change(kp, sp, k, s, h, B)
     per = got[3:].reshape(-1, 3)
     assert per.shape[0] == 4 * 2 * 3
     want_tau = np.zeros(per.shape[0], np.float32)
-    want_tau[23] = 0.125       # h |delta|, exact in binary
+    want_tau[23] = dtrans
     want_s = np.zeros(per.shape[0], np.float32)
     want_s[4] = 1.0
     np.testing.assert_array_equal(per[:, 0], want_tau)
     np.testing.assert_array_equal(per[:, 1], want_s)
     np.testing.assert_array_equal(per[:, 2], np.float32(3.0))
-    np.testing.assert_array_equal(got[:3], np.float32([0.125, 1.0, 3.0]))
+    np.testing.assert_array_equal(got[:3], np.array([dtrans, 1.0, 3.0], np.float32))
 
 
 def test_unchanged_fields_give_zero_change_and_the_source_scale():
