@@ -310,6 +310,93 @@ def point_source_measurement(kappa, shape, h, flush, reps: int = 10):
             "rate": n / (t * 1e-3) / 1e9, "rate_unit": "G cells/s"}
 
 
+def reuse_measurement(ctx, flush, steps: int = 12, cells_per_step: float = 0.01, reps: int = 10):
+    """Reuse of f across time steps (paper Sec. 7; vet_field_change and
+    vet.ClosureReuse) on the workload's lognormal fields carried 0.01 cells
+    per step: per tolerance the steps that recompute, the time per step
+    (gate, 12-byte read-back and the closures it runs) and the largest
+    difference from a fresh f; and the gate kernel against the HBM copy
+    bandwidth on the fields repeated 8 times along z (L2 flushed before
+    every timed launch; 16 bytes read per cell, 24 with the snapshot)."""
+    import torch
+
+    from paper_2202_08778_gb300 import synth, vet
+
+    p, seq = synth.lognormal_sequence(n=128, B=16, nside=4, seed=2, steps=steps, cells_per_step=cells_per_step)
+    dev = flush.device
+    fields = [(torch.from_numpy(k.ravel()).to(dev), torch.from_numpy(s.ravel()).to(dev)) for k, s in seq]
+    n = ctx.ncell
+    fresh = []
+    for k, s in fields:
+        f = torch.empty(6 * n, dtype=torch.float32, device=dev)
+        ctx.closure(k, s, None, f)
+        fresh.append(f)
+    torch.cuda.synchronize(dev)
+    runs = []
+    for tol in (0.0, 0.02, 0.05, 0.1):
+        run = vet.ClosureReuse(ctx, tol_tau=tol, tol_S=tol, max_age=8)
+        err = []
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for t, (k, s) in enumerate(fields):
+            f, _ = run.step(k, s)
+        torch.cuda.synchronize(dev)
+        dt = (time.perf_counter() - t0) / steps
+        run2 = vet.ClosureReuse(ctx, tol_tau=tol, tol_S=tol, max_age=8)
+        flags = []
+        for t, (k, s) in enumerate(fields):  # same decisions, errors taken outside the timed loop
+            f, redo = run2.step(k, s)
+            flags.append(bool(redo))
+            err.append(float((f - fresh[t]).abs().max()))
+        runs.append({"tol": tol, "recomputed_steps": [i for i, r in enumerate(flags) if r],
+                     "ms_per_step": 1e3 * dt, "cell_angle_per_s_G": n * ctx.N / dt / 1e9,
+                     "max_abs_df": max(err), "max_abs_df_per_step": err})
+    # the gate kernel alone, on 8 copies of the fields stacked along z
+    k0, s0 = fields[0]
+    k1, s1 = fields[1]
+    nz, ny, nx = ctx.shape
+    big = [x.repeat(8) for x in (k1, s1, k0, s0)]
+    nb = 8 * n // ctx.block ** 3
+    out = torch.empty(3 + 3 * nb, dtype=torch.float32, device=dev)
+    res = {}
+    for snap in (False, True):
+        ms = []
+        for r in range(reps + 3):
+            flush.fill_(r & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            vet.field_change((8 * nz, ny, nx), ctx.block, ctx.h, *big, out, snap)
+            b.record()
+            torch.cuda.synchronize(dev)
+            if r >= 3:
+                ms.append(a.elapsed_time(b))
+        res[snap] = statistics.median(ms)
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    gbs = 16.0 * 8 * n / (res[False] * 1e-3) / 1e9
+    gbs_snap = 24.0 * 8 * n / (res[True] * 1e-3) / 1e9
+    ms1 = []
+    kr, sr = k0.clone(), s0.clone()
+    out1 = torch.empty(3 + 3 * (n // ctx.block ** 3), dtype=torch.float32, device=dev)
+    for r in range(reps + 3):
+        flush.fill_(r & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        vet.field_change(ctx.shape, ctx.block, ctx.h, k1, s1, kr, sr, out1, False)
+        b.record()
+        torch.cuda.synchronize(dev)
+        if r >= 3:
+            ms1.append(a.elapsed_time(b))
+    return {"workload": f"lognormal128 fields carried {cells_per_step} cells per step, {steps} steps",
+            "runs": runs, "max_age": 8,
+            "gate": {"kernel": "gate_kernel<true> (vet_field_change)", "cells": 8 * n,
+                     "input": "two steps' fields repeated 8 times along z", "ms": res[False],
+                     "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                     "algorithmic": "16 bytes read per cell (kappa, S, kappa_ref, S_ref)",
+                     "snapshot": {"ms": res[True], "achieved": gbs_snap, "frac": gbs_snap / peak,
+                                  "algorithmic": "16 bytes read and 8 written per cell"},
+                     "us_at_128cubed": 1e3 * statistics.median(ms1)}}
+
+
 def learned_measurement(local_rank):
     """The learned closure at 256^3 in 16^3 blocks with 192 directions (the
     lognormal generator, seed 3) against the plain closure on the same GPU.
@@ -533,6 +620,9 @@ def run_ours(args, rank, world, local_rank):
     if clocks is not None:
         line["clocks"] = clocks
 
+    if rank == 0 and world == 1 and not args.no_reuse:
+        line["reuse"] = reuse_measurement(ctx, flush)
+
     if rank == 0 and world == 1 and not args.no_batch:
         line["batch"] = batch_measurement(local_rank)
 
@@ -558,6 +648,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-grid batched-closure measurement")
+    ap.add_argument("--no-reuse", action="store_true", help="skip the measurement of reusing f across time steps")
     ap.add_argument("--tuning", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
                     metavar="FG,DT", help="fixed face-pass direction group and cell-pass direction tile "
                     "instead of autotuning")

@@ -347,6 +347,35 @@ vet_status vet_point_source(const vet_grid *grid, const double xs[3], double L, 
                             float *pdot_out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Change gate for reusing the Eddington tensor across time steps (paper
+ * Sec. 7, "Performance": f may be recomputed only every few time steps).
+ * Measures how far the closure's inputs moved since a snapshot, per block of
+ * grid->block^3 cells and over the grid:
+ *   dtrans = max |a - b| / ((1 + a/2) (1 + b/2)),  a = kappa h, b = kappa_ref h
+ *            (a bound on the change |e^{-a} - e^{-b}| of a cell's
+ *            transmission, which moves the intensity leaving the cell:
+ *            ~ |a - b| for thin cells, small for thick ones)
+ *   dS     = max |S - S_ref|    (largest change of the source)
+ *   Sref   = max |S_ref|        (scale of the source)
+ * computed in FP32, each operation one IEEE rounding (h as (float)h) and a
+ * maximum exact, so the result is the same for any reduction order.  A NaN
+ * (in a difference, the quotient or S_ref) counts as +inf.
+ * out: device float [3 + 3 * blocks]: out[0..2] the grid's (dtrans, dS, Sref),
+ * then each block's triple, blocks x-fastest (b = (bk * nby + bj) * nbx + bi).
+ * With snapshot != 0 the same pass also copies kappa into kappa_ref and S
+ * into S_ref; out then describes the change before the copy.  The decision
+ * (recompute when dtrans or dS / Sref exceeds a tolerance, or the stored f is
+ * too old) is the caller's.
+ * grid: cells, block edge (2..32, dividing every extent) and h; kappa, S,
+ * kappa_ref, S_ref: [nz][ny][nx] device memory, caller-owned, the two
+ * snapshot arrays not overlapping the others.  Work is enqueued on `stream`
+ * (out[0..2] is cleared on the stream first).  VET_EINVAL for a bad grid or a
+ * missing or host pointer; VET_ECUDA for a failed launch.  Needs no context.
+ * ---------------------------------------------------------------------- */
+vet_status vet_field_change(const vet_grid *grid, const float *kappa, const float *S, float *kappa_ref, float *S_ref,
+                            int snapshot, float *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * An entry point that allocates nothing (the paper has no counterpart; it
  * exists for callers of this library, not for the method).
  *

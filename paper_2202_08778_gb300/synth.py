@@ -143,3 +143,47 @@ def batched_problems(n_grids: int = 64, seed0: int = 100, edges=(32, 48, 64, 80,
         nside = int(rng.choice(nsides))
         out.append(lognormal_problem(n=n, B=B, nside=nside, seed=seed0 + g))
     return out
+
+
+def _shift(g: np.ndarray, disp) -> np.ndarray:
+    """g(x - disp) of a periodic field (disp in cells per axis, (x, y, z)),
+    by a phase shift in Fourier space (exact for a band-limited field)."""
+    nz, ny, nx = g.shape
+    gk = np.fft.rfftn(g)
+    kz = np.fft.fftfreq(nz)[:, None, None]
+    ky = np.fft.fftfreq(ny)[None, :, None]
+    kx = np.fft.rfftfreq(nx)[None, None, :]
+    phase = np.exp(-2j * math.pi * (kx * disp[0] + ky * disp[1] + kz * disp[2]))
+    return np.fft.irfftn(gk * phase, s=g.shape, axes=(0, 1, 2))
+
+
+def lognormal_sequence(n: int = 128, B: int = 16, nside: int = 4, seed: int = 2, steps: int = 8,
+                       cells_per_step: float = 0.05, direction=(1.0, 0.6, 0.3), **kw):
+    """Time sequence of the lognormal workload for the reuse of f across time
+    steps: the two Gaussian fields behind kappa and T are carried along
+    ``direction`` by ``cells_per_step`` cells per step (periodic), the
+    recipe of ``lognormal_problem`` applied to each shifted pair.  Returns
+    the step-0 problem dict (its kappa, S are step 0's) and a list of
+    (kappa, S) float32 arrays, one per step."""
+    p = lognormal_problem(n=n, B=B, nside=nside, seed=seed, **kw)
+    shape = p["kappa"].shape
+    rng = np.random.default_rng(seed)
+    g1 = gaussian_random_field(shape, rng)
+    g2 = gaussian_random_field(shape, rng)
+    sig_k = kw.get("sigma_ln_kappa", 1.5)
+    sig_t = kw.get("sigma_ln_T", 0.5)
+    rho = kw.get("rho", 0.5)
+    med = kw.get("median_dtau", 10 ** -0.5)
+    clip = kw.get("dtau_clip", (1e-3, 1e2))
+    d = np.asarray(direction, float)
+    d /= np.linalg.norm(d)
+    seq = []
+    for t in range(steps):
+        disp = d * cells_per_step * t
+        a1 = g1 if t == 0 else _shift(g1, disp)
+        a2 = g2 if t == 0 else _shift(g2, disp)
+        dtau = np.clip(np.exp(math.log(med) + sig_k * a1), clip[0], clip[1])
+        lnT = sig_t * (rho * a1 + math.sqrt(1.0 - rho * rho) * a2)
+        seq.append((np.ascontiguousarray((dtau / p["h"]).astype(np.float32)),
+                    np.ascontiguousarray((np.exp(4.0 * lnT) / FOUR_PI).astype(np.float32))))
+    return p, seq

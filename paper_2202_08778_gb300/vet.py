@@ -33,7 +33,7 @@ EXPORTS = (
     "vet_model_create", "vet_model_destroy", "vet_model_num_params", "vet_model_set_params", "vet_model_get_params",
     "vet_model_get_grads", "vet_model_features", "vet_model_forward", "vet_model_backward", "vet_model_step",
     "vet_closure_learned", "vet_model_last_timing", "vet_model_last_indicator", "vet_model_last_error",
-    "vet_local_closure", "vet_point_source",
+    "vet_local_closure", "vet_point_source", "vet_field_change",
 )
 
 #: functions whose return value is not a vet_status
@@ -130,6 +130,7 @@ def load(build_if_missing: bool = True):
         lib.vet_local_closure.argtypes = [i, ctypes.c_longlong, vp, vp, vp]
         lib.vet_point_source.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                          vp, vp, vp, vp]
+        lib.vet_field_change.argtypes = [ctypes.POINTER(_Grid), vp, vp, vp, vp, i, vp, vp]
         for name in EXPORTS:
             if name not in _NOT_STATUS:
                 getattr(lib, name).restype = ctypes.c_int
@@ -316,6 +317,101 @@ def point_source(shape, h: float, xs, L: float, kappa, Edot_out, pdot_out=None, 
     if st != VET_OK:
         raise VetError(st, "vet_point_source")
     return Edot_out
+
+
+def field_change(shape, block: int, h: float, kappa, S, kappa_ref, S_ref, out, snapshot: bool = False,
+                 stream=None):
+    """vet_field_change: per block of block^3 cells and over the grid, the
+    largest bound on the change of a cell's transmission, |a - b| / ((1 +
+    a/2)(1 + b/2)) with a = kappa h and b = kappa_ref h, the largest change of
+    the source |S - S_ref| and the source scale max |S_ref| (FP32; out [3 + 3
+    * blocks], the grid's triple first, blocks x-fastest).  With snapshot the
+    same pass copies kappa, S into kappa_ref, S_ref.  Device tensors."""
+    lib = load()
+    nz, ny, nx = shape
+    n = int(nz) * int(ny) * int(nx)
+    B = int(block)
+    nb = n // (B * B * B) if B > 0 else 0
+    g = _Grid(int(nx), int(ny), int(nz), B, float(h))
+    st = lib.vet_field_change(ctypes.byref(g), _ptr(kappa, np.float32, n, "kappa"), _ptr(S, np.float32, n, "S"),
+                              _ptr(kappa_ref, np.float32, n, "kappa_ref"), _ptr(S_ref, np.float32, n, "S_ref"),
+                              int(bool(snapshot)), _ptr(out, np.float32, 3 + 3 * nb, "out"), _stream(stream))
+    if st != VET_OK:
+        raise VetError(st, "vet_field_change")
+    return out
+
+
+def reuse_decision(change, age: int, first: bool, tol_tau: float, tol_S: float, max_age: int) -> bool:
+    """Whether a stored Eddington tensor must be recomputed this time step
+    (paper Sec. 7): always on the first step and once it is max_age steps
+    old; otherwise when the grid's largest transmission change exceeds
+    tol_tau or its largest source change exceeds tol_S times the source
+    scale.  `change` is the grid triple (dtrans, dS, Sref) of field_change;
+    a non-finite change forces a recompute."""
+    if first or age >= max_age:
+        return True
+    dtr, dS, sref = float(change[0]), float(change[1]), float(change[2])
+    if dtr != dtr or dS != dS or dtr == float("inf") or dS == float("inf"):
+        return True
+    return dtr > tol_tau or dS > tol_S * sref
+
+
+class ClosureReuse:
+    """Time steps of the closure that reuse f while its inputs stay close to
+    the snapshot f was computed from (paper Sec. 7's suggestion of updating
+    the Eddington tensor only every few steps).  Each step runs the change
+    gate (vet_field_change) against the snapshot, reads the grid's three
+    numbers back to the host (12 bytes; the step synchronises the stream),
+    and either keeps the stored f or recomputes it with the context and takes
+    a new snapshot.  Owns the snapshot and f (device, FP32).
+
+    The boundary intensities are not watched: pass force=True on a step
+    whose Ib differs from the one f was computed with."""
+
+    def __init__(self, ctx: Context, tol_tau: float = 5e-2, tol_S: float = 5e-2, max_age: int = 8):
+        import torch
+
+        if ctx.precision != VET_FP32:
+            raise ValueError("ClosureReuse needs an FP32 context")
+        if max_age < 1:
+            raise ValueError("max_age must be at least 1")
+        self.ctx, self.tol_tau, self.tol_S, self.max_age = ctx, float(tol_tau), float(tol_S), int(max_age)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n, B = ctx.ncell, ctx.block
+        self.kappa_ref = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.S_ref = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.change = torch.zeros(3 + 3 * (n // (B * B * B)), dtype=torch.float32, device=dev)
+        self._host = torch.zeros(3, dtype=torch.float32).pin_memory()
+        self.f = torch.zeros(6 * n, dtype=torch.float32, device=dev)
+        self.age, self.first = 0, True
+        self.recomputes = 0
+        self.last_change = (0.0, 0.0, 0.0)
+
+    def step(self, kappa, S, Ib=None, M_out=None, force: bool = False, stream=None):
+        """One time step: returns (f, recomputed).  M_out, if given, is
+        written only on steps that recompute."""
+        import torch
+
+        st = _stream(stream)
+        if not self.first:
+            field_change(self.ctx.shape, self.ctx.block, self.ctx.h, kappa, S, self.kappa_ref, self.S_ref,
+                         self.change, False, st)
+            s = torch.cuda.ExternalStream(st) if st else torch.cuda.current_stream()
+            with torch.cuda.stream(s):
+                self._host.copy_(self.change[:3], non_blocking=True)
+            s.synchronize()
+            self.last_change = tuple(float(v) for v in self._host)
+        redo = force or reuse_decision(self.last_change, self.age, self.first, self.tol_tau, self.tol_S,
+                                       self.max_age)
+        if redo:
+            self.ctx.closure(kappa, S, Ib, self.f, M_out, stream=st)
+            field_change(self.ctx.shape, self.ctx.block, self.ctx.h, kappa, S, self.kappa_ref, self.S_ref,
+                         self.change, True, st)
+            self.age, self.first = 0, False
+            self.recomputes += 1
+        else:
+            self.age += 1
+        return self.f, redo
 
 
 def closure_noalloc(shape, block: int, h: float, nside: int, kappa, S, Ib, f_out, M_out=None,

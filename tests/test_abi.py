@@ -50,3 +50,13 @@ def test_create_without_gpu_fails_cleanly():
         assert e.status == vet.VET_ECUDA
     else:  # pragma: no cover
         raise AssertionError("vet_create succeeded without a GPU")
+
+
+def test_binding_declares_argument_types_of_every_entry_point():
+    """Without argtypes ctypes passes Python ints as 32-bit C ints, which
+    truncates 64-bit device pointers."""
+    from paper_2202_08778_gb300 import vet
+
+    lib = vet.load()
+    for n in vet.EXPORTS:
+        assert getattr(lib, n).argtypes is not None, n
