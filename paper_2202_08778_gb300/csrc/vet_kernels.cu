@@ -843,6 +843,13 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     for (int m = 0; m < 4; ++m) cmp[r][m] = 0.f;
   }
 
+  // plain FP32 partial sums over four tiles, folded into the compensated
+  // sums after the fourth (or the last) tile
+  float part_[2][10];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int m = 0; m < 10; ++m) part_[r][m] = 0.f;
   bool ok = true;
   for (int t = 0; t < ntiles && ok; ++t) {
     const int b = t & 1;
@@ -851,11 +858,6 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
     consumed = t + 1;
     const int nd = min(dt, g.ndir - t * dt);
     const unsigned char *buf = buf0 + (size_t)b * dt * sb;
-    float part_[2][10];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-      for (int m = 0; m < 10; ++m) part_[r][m] = 0.f;
     // every cell needs both members of a pair: (c, d) with (c', -d), then
     // (c, -d) with (c', d), the primary direction's template driving each
     for (int jj = 0; jj < nd; ++jj) {
@@ -927,7 +929,7 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
           }
       }
     }
-    if (MODE != 1) {
+    if (MODE != 1 && ((t & 3) == 3 || t + 1 == ntiles)) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
 #pragma unroll
@@ -946,6 +948,8 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
         mom[r][7] += part_[r][7];
         mom[r][8] += part_[r][8];
         mom[r][9] += part_[r][9];
+#pragma unroll
+        for (int m = 0; m < 10; ++m) part_[r][m] = 0.f;
       }
     }
     __syncwarp();
