@@ -173,11 +173,15 @@ vet_status build_context(vet_ctx *c) {
   if (!c->fp64 && (B == 8 || B == 16) && vet::geom::antipodal_order(N, c->dirs_ext.data(), order.data(),
                                                                      cell_order.data())) {
     c->dims.paired = 1;
-    // pairs whose templates are not exact mirrors are marched ray by ray
+    // pairs whose templates are not exact mirrors, or with a zero direction
+    // component (whose sign the antipode need not flip), are marched ray by ray
     for (int k = 0; k < N; k += 2) {
       unsigned char *ta = tpl.data() + (size_t)cell_order[k] * tbytes;
       unsigned char *tb = tpl.data() + (size_t)cell_order[k + 1] * tbytes;
-      const int m = vet::geom::mirror_templates<R>(ta, tb, B) ? 1 : 0;
+      const vet::TplHead<R> *ha = reinterpret_cast<const vet::TplHead<R> *>(ta);
+      const vet::TplHead<R> *hb = reinterpret_cast<const vet::TplHead<R> *>(tb);
+      const bool flips = ha->sgn[0] == -hb->sgn[0] && ha->sgn[1] == -hb->sgn[1] && ha->sgn[2] == -hb->sgn[2];
+      const int m = flips && vet::geom::mirror_templates<R>(ta, tb, B) ? 1 : 0;
       reinterpret_cast<vet::TplHead<R> *>(ta)->mirror = m;
       reinterpret_cast<vet::TplHead<R> *>(tb)->mirror = m;
     }

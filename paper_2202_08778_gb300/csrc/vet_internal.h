@@ -41,6 +41,7 @@ struct TplHead {
   int sgn[3]; // +1 if n_a >= 0 (a zero component counts as positive) else -1
   int ext;    // index of this direction in the documented HEALPix order
   int mirror; // 1: this template and its antipode's are exact mirror images
+              // and every sign flips (no zero component)
               // (same event lengths, negated offsets, same exit tables)
   // quadrature coefficients w (1, nx, ny, nz, nx nx, ny ny, nz nz, nx ny,
   // nx nz, ny nz) of E, F and P (Eqs. 10-12, c = 1), rounded once from FP64;

@@ -866,23 +866,24 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
       const TplHead<float> *H2 = reinterpret_cast<const TplHead<float> *>(buf + sb * j2);  // its antipode
       const float *fin1 = reinterpret_cast<const float *>(buf + sb * j1 + TL.bytes);
       const float *fin2 = reinterpret_cast<const float *>(buf + sb * j2 + TL.bytes);
+      // upwind-frame coordinates of the cell in d; on a mirrored pair (every
+      // sign flips) the mirror cell in -d has the same ones, since each
+      // coordinate c becomes B - 1 - c, so both rays share them, their exit
+      // and their face index
       const int l0 = T.h->sgn[0] > 0 ? cx : B - 1 - cx;
       const int l1 = T.h->sgn[1] > 0 ? cy : B - 1 - cy;
       const int l2 = T.h->sgn[2] > 0 ? cz : B - 1 - cz;
-      const int m0 = H2->sgn[0] > 0 ? mx : B - 1 - mx;
-      const int m1 = H2->sgn[1] > 0 ? my : B - 1 - my;
-      const int m2 = H2->sgn[2] > 0 ? mz : B - 1 - mz;
       float I1, I2;
       if (T.h->mirror) {
         const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
-        int last = p0, ae = 0, la = l0, lb = l1, lc = l2, nb_ = m1, nc_ = m2;
-        if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; nb_ = m0; }
-        if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; nb_ = m0; nc_ = m1; }
+        int last = p0, ae = 0, la = l0, lb = l1, lc = l2;
+        if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; }
+        if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; }
         const int row = (ae * 2) * B + la;
         const int kb = T.ck[row], kc = T.ck[row + B];
         const float2 wb = T.cw[row], wc = T.cw[row + B];
         const float Iin1 = face_value<float>(fin1, fstride, B, ae, lb, lc, kb, kc, wb, wc);
-        const float Iin2 = face_value<float>(fin2, fstride, B, ae, nb_, nc_, kb, kc, wb, wc);
+        const float Iin2 = face_value<float>(fin2, fstride, B, ae, lb, lc, kb, kc, wb, wc);
         uint64_t I = pk2(Iin1, Iin2);
         // aligned at the downwind end; once the event index reaches the
         // warp's smallest `last` every lane marches and the identity
@@ -914,6 +915,9 @@ __global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
         // differently): each ray follows its own direction's template
         const Tpl<float> T2(buf + sb * j2, TL);
         I1 = cell_ray4(T, fin1, fstride, B, l0, l1, l2, t1);
+        const int m0 = H2->sgn[0] > 0 ? mx : B - 1 - mx;
+        const int m1 = H2->sgn[1] > 0 ? my : B - 1 - my;
+        const int m2 = H2->sgn[2] > 0 ? mz : B - 1 - mz;
         I2 = cell_ray4(T2, fin2, fstride, B, m0, m1, m2, t2);
       }
       if (MODE == 1) {
