@@ -366,6 +366,20 @@ inline bool mirror_templates(const unsigned char *ta, const unsigned char *tb, i
                             tb + L.cw, B);
 }
 
+// Whether the paired cell pass may march an antipodal pair as one mirrored
+// pair: the cell c in d and the mirror cell B - 1 - c in -d then share their
+// upwind-frame coordinates, exit and face index, which needs every sign to
+// flip (a zero component counts as positive, so a direction with one keeps
+// that sign in its antipode) and the cell-ray templates to be exact mirrors.
+template <typename R>
+inline bool mirrored_cell_pair(const unsigned char *ta, const unsigned char *tb, int B) {
+  const TplHead<R> *ha = reinterpret_cast<const TplHead<R> *>(ta);
+  const TplHead<R> *hb = reinterpret_cast<const TplHead<R> *>(tb);
+  for (int a = 0; a < 3; ++a)
+    if (ha->sgn[a] != -hb->sgn[a]) return false;
+  return mirror_templates<R>(ta, tb, B);
+}
+
 // Face-pass schedule: level L of block b in octant o is b's upwind-ordered
 // index sum; one item = (block, up to `group` directions of one octant), or
 // up to level_group[L] directions on level L when that table is given.

@@ -178,10 +178,7 @@ vet_status build_context(vet_ctx *c) {
     for (int k = 0; k < N; k += 2) {
       unsigned char *ta = tpl.data() + (size_t)cell_order[k] * tbytes;
       unsigned char *tb = tpl.data() + (size_t)cell_order[k + 1] * tbytes;
-      const vet::TplHead<R> *ha = reinterpret_cast<const vet::TplHead<R> *>(ta);
-      const vet::TplHead<R> *hb = reinterpret_cast<const vet::TplHead<R> *>(tb);
-      const bool flips = ha->sgn[0] == -hb->sgn[0] && ha->sgn[1] == -hb->sgn[1] && ha->sgn[2] == -hb->sgn[2];
-      const int m = flips && vet::geom::mirror_templates<R>(ta, tb, B) ? 1 : 0;
+      const int m = vet::geom::mirrored_cell_pair<R>(ta, tb, B) ? 1 : 0;
       reinterpret_cast<vet::TplHead<R> *>(ta)->mirror = m;
       reinterpret_cast<vet::TplHead<R> *>(tb)->mirror = m;
     }

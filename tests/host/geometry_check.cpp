@@ -3,13 +3,17 @@
 //  - the cell- and node-ray parts of each antipodal pair's templates are
 //    exact mirrors (rotated sets), and a template is not the mirror of a
 //    direction other than its antipode;
+//  - the paired cell pass marches every antipodal pair of a rotated set as a
+//    mirrored pair, and never one with a zero direction component (whose
+//    sign the antipode keeps) of the unrotated set;
 //  - the paired face-pass schedule, with each item's point-mirrored block and
 //    antipodal directions added, lists every (block, direction) of the
 //    unpaired schedule exactly once, level by level.
 // Usage: geometry_check nbx nby nbz B nside [unrotated]   (prints "ok" or the
 // failure).  The rotation is a generic one (irrational components: no two
 // plane crossings of a direction tie); "unrotated" checks instead that the
-// HEALPix set itself, with its z = 0 ring, is refused.
+// HEALPix set itself, with its z = 0 ring, is refused by the face pass's
+// mirror order and its zero-component pairs by the cell pass's pairing.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -38,10 +42,40 @@ int main(int argc, char **argv) {
   std::vector<int> order(N);
   int ob[9];
   vet::geom::internal_order(N, d.data(), order.data(), ob);
+  const int tb = vet::tpl_layout<float>(B).bytes;
+  std::vector<unsigned char> tpl((size_t)tb * N);
+  auto T = [&](int i) { return tpl.data() + (size_t)i * tb; };
+  auto build_templates = [&]() {
+    for (int i = 0; i < N; ++i) {
+      long long cs, ns[3];
+      vet::geom::build_template<float>(&d[4 * order[i]], order[i], B, 0.01, T(i), cs, ns);
+    }
+  };
+  // the paired cell pass: pairs (cell_order[2k], cell_order[2k + 1]) of antipodes
+  auto check_cell_pairs = [&](bool rotated) -> int {
+    std::vector<int> cell_order(N);
+    vet::geom::interleaved_order(ob, cell_order.data());
+    if (!vet::geom::antipodal_order(N, d.data(), order.data(), cell_order.data()))
+      return fail("antipodal_order refused a set closed under negation");
+    int zero_pairs = 0;
+    for (int k = 0; k < N; k += 2) {
+      const int i = cell_order[k], j = cell_order[k + 1];
+      const double *a = &d[4 * order[i]];
+      const bool zero = a[0] == 0.0 || a[1] == 0.0 || a[2] == 0.0;
+      const bool m = vet::geom::mirrored_cell_pair<float>(T(i), T(j), B);
+      if (zero && m) return fail("a pair with a zero direction component was marked mirrored");
+      if (rotated && !m) return fail("an antipodal pair of a rotated set was not marked mirrored");
+      zero_pairs += zero ? 1 : 0;
+    }
+    if (!rotated && zero_pairs == 0) return fail("the unrotated set has no zero component to check");
+    return 0;
+  };
   if (unrotated) {
     const std::vector<int> before = order;
     if (vet::geom::mirror_octant_order(N, d.data(), order.data(), ob)) return fail("a set with zero components was paired");
     if (order != before) return fail("a refused mirror order changed the order");
+    build_templates();
+    if (check_cell_pairs(false)) return 1;
     std::printf("ok\n");
     return 0;
   }
@@ -52,13 +86,8 @@ int main(int argc, char **argv) {
       if (std::fabs(a[0] + b[0]) + std::fabs(a[1] + b[1]) + std::fabs(a[2] + b[2]) > 1e-12)
         return fail("octant positions do not hold antipodes");
     }
-  const int tb = vet::tpl_layout<float>(B).bytes;
-  std::vector<unsigned char> tpl((size_t)tb * N);
-  for (int i = 0; i < N; ++i) {
-    long long cs, ns[3];
-    vet::geom::build_template<float>(&d[4 * order[i]], order[i], B, 0.01, tpl.data() + (size_t)i * tb, cs, ns);
-  }
-  auto T = [&](int i) { return tpl.data() + (size_t)i * tb; };
+  build_templates();
+  if (check_cell_pairs(true)) return 1;
   for (int o = 0; o < 8; o += 2)
     for (int k = 0; k < ob[o + 1] - ob[o]; ++k) {
       const int i = ob[o] + k, j = ob[7 - o] + k;
