@@ -236,7 +236,7 @@ def batch_measurement(local_rank, reps: int = 20):
 
 
 def local_closure_measurement(ctx, kappa, S, flush, reps: int = 20):
-    """The M1 local closure (paper Sec. 6.1; vet_local_closure) on the
+    """The M1 local closure (paper Sec. 4.1; vet_local_closure) on the
     moments of this workload, against the HBM copy bandwidth: 16 bytes read
     and 24 written per cell, L2 flushed before every timed launch."""
     import torch
@@ -311,7 +311,7 @@ def point_source_measurement(kappa, shape, h, flush, reps: int = 10):
 
 
 def reuse_measurement(ctx, flush, steps: int = 12, cells_per_step: float = 0.01, reps: int = 10):
-    """Reuse of f across time steps (paper Sec. 7; vet_field_change and
+    """Reuse of f across time steps (paper Sec. 4.2; vet_field_change and
     vet.ClosureReuse) on the workload's lognormal fields carried 0.01 cells
     per step: per tolerance the steps that recompute, the time per step
     (gate, 12-byte read-back and the closures it runs) and the largest

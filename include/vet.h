@@ -111,8 +111,12 @@ vet_status vet_trace(vet_ctx *ctx, const float *kappa, const float *S, const flo
                      void *stream);
 
 /* Angular quadratures of given intensities (Eqs. 10-12, c = 1):
- * I[N][cells] -> M_out[10][cells].  FP32 context only. */
-vet_status vet_moments(vet_ctx *ctx, const float *I, float *M_out, void *stream);
+ * I[N][cells] -> M_out[10][cells].  E64_out (optional, NULL to skip; DEVICE
+ * memory, [cells]) also receives E summed in FP64 (the weights are all
+ * 4 pi / N, so E64 = (4 pi / N) sum_k I_k accumulated in double), for callers
+ * that guard f where E is far below its neighbours.  FP32 context only;
+ * VET_EINVAL if E64_out is not device memory. */
+vet_status vet_moments(vet_ctx *ctx, const float *I, float *M_out, double *E64_out, void *stream);
 
 /* Whole closure, fused: trace + quadratures + f = P/E (Eq. 13) without
  * storing I.  f_out[6][cells] required; M_out[10][cells] optional (NULL).
@@ -175,9 +179,11 @@ vet_status vet_autotune(vet_ctx *ctx, const float *kappa, const float *S, const 
  * Batches of independent grids (ragged sizes, block edges and direction
  * sets).  Each grid gets its own context (vet_create); vet_batch_closure
  * runs one closure per grid, each on its own branch of one CUDA graph that is
- * captured on the first call and replayed while the field pointers stay the
- * same, so the grids' kernels run concurrently and the whole batch costs one
- * graph launch.  FP32, one device, device pointers only.
+ * captured on the first call and replayed while the field pointers and the
+ * members' tunings stay the same (retuning a member through
+ * vet_batch_context makes the next call capture again), so the grids'
+ * kernels run concurrently and the whole batch costs one graph launch.  FP32,
+ * one device, device pointers only.
  * ---------------------------------------------------------------------- */
 typedef struct vet_batch vet_batch;
 
@@ -252,6 +258,17 @@ vet_status vet_model_get_params(vet_model *model, float *params);
  * layout as the parameters). */
 vet_status vet_model_get_grads(vet_model *model, float *grads);
 
+/* Checkpoint of a model to a file and back: the parameters, AdamW's two
+ * moment estimates and its step count, so that training resumes where it
+ * stopped.  Format: the 8 bytes "VETMODL1", int32 hidden channels, int32 0,
+ * int64 parameter count, int64 step count, then three FP32 arrays in the host
+ * parameter layout above (parameters, first moments, second moments),
+ * little-endian.  load checks the tag, the hidden width and the parameter
+ * count (VET_EINVAL on a mismatch, an unreadable or truncated file; the model
+ * is then unchanged) and synchronises the device.  Not in the paper. */
+vet_status vet_model_save(vet_model *model, const char *path);
+vet_status vet_model_load(vet_model *model, const char *path);
+
 /* Features of `nvol` volumes of the grid (each [nz][ny][nx], stacked) into
  * the model's workspace: kappa, S, E are [nvol][nz][ny][nx]; grid->block is
  * the block of the block statistics and must divide every extent.
@@ -307,7 +324,7 @@ const char *vet_model_last_error(const vet_model *model);
 const char *vet_last_error(const vet_ctx *ctx);
 
 /* ------------------------------------------------------------------------
- * Local closures (paper Sec. 6.1, the comparison with FLD and M1): the
+ * Local closures (paper Sec. 4.1, the comparison with FLD and M1): the
  * Eddington tensor of each cell from that cell's moments alone.
  *   VET_CLOSURE_EDDINGTON: T = I / 3 (M may be NULL).
  *   VET_CLOSURE_M1:        T = (1 - chi)/2 I + (3 chi - 1)/2 n n with
@@ -348,7 +365,7 @@ vet_status vet_point_source(const vet_grid *grid, const double xs[3], double L, 
 
 /* ------------------------------------------------------------------------
  * Change gate for reusing the Eddington tensor across time steps (paper
- * Sec. 7, "Performance": f may be recomputed only every few time steps).
+ * Sec. 4.2, "Performance": f may be recomputed only every few time steps).
  * Measures how far the closure's inputs moved since a snapshot, per block of
  * grid->block^3 cells and over the grid:
  *   dtrans = max |a - b| / ((1 + a/2) (1 + b/2)),  a = kappa h, b = kappa_ref h
@@ -363,9 +380,11 @@ vet_status vet_point_source(const vet_grid *grid, const double xs[3], double L, 
  * out: device float [3 + 3 * blocks]: out[0..2] the grid's (dtrans, dS, Sref),
  * then each block's triple, blocks x-fastest (b = (bk * nby + bj) * nbx + bi).
  * With snapshot != 0 the same pass also copies kappa into kappa_ref and S
- * into S_ref; out then describes the change before the copy.  The decision
- * (recompute when dtrans or dS / Sref exceeds a tolerance, or the stored f is
- * too old) is the caller's.
+ * into S_ref; out then describes the change before the copy.
+ * dtrans bounds the change of the transmission across one cell EDGE (optical
+ * depth kappa h); a ray crossing a cell diagonally travels up to sqrt(3) h,
+ * so its transmission may change by up to about sqrt(3) times dtrans: a
+ * tolerance on dtrans is a tolerance per cell edge.
  * grid: cells, block edge (2..32, dividing every extent) and h; kappa, S,
  * kappa_ref, S_ref: [nz][ny][nx] device memory, caller-owned, the two
  * snapshot arrays not overlapping the others.  Work is enqueued on `stream`
@@ -374,6 +393,18 @@ vet_status vet_point_source(const vet_grid *grid, const double xs[3], double L, 
  * ---------------------------------------------------------------------- */
 vet_status vet_field_change(const vet_grid *grid, const float *kappa, const float *S, float *kappa_ref, float *S_ref,
                             int snapshot, float *out, void *stream);
+
+/* The reuse decision for one time step (paper Sec. 4.2, which suggests
+ * recomputing f only every few steps and gives no criterion; this is the
+ * library's reading): *recompute = 1 on the first step (first != 0), once
+ * the stored f is max_age steps old (age >= max_age), when dtrans or dS is
+ * not finite, or when dtrans > tol_tau or dS > tol_S * Sref; else 0.
+ * change: HOST float[3], the grid triple (dtrans, dS, Sref) of
+ * vet_field_change copied back; the comparisons are made in double on those
+ * FP32 values.  Host only, no GPU work.  VET_EINVAL for a NULL pointer,
+ * max_age < 1, age < 0 or a negative or NaN tolerance. */
+vet_status vet_reuse_decision(const float *change, int age, int first, double tol_tau, double tol_S, int max_age,
+                              int *recompute);
 
 /* ------------------------------------------------------------------------
  * An entry point that allocates nothing (the paper has no counterpart; it

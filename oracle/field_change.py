@@ -1,5 +1,5 @@
 """Oracle of the change gate for reusing the Eddington tensor across time
-steps (paper Sec. 7, "Performance": the suggestion that f need not be
+steps (paper Sec. 4.2, "Performance": the suggestion that f need not be
 recomputed at the start of every time step).
 
 TEST INFRASTRUCTURE: imported only by the tests and the benchmark; it shares

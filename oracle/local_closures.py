@@ -1,5 +1,5 @@
 """FP64 oracle of the two local closures the paper compares the VET with
-(Sec. 6.1, "Comparison to FLD and M1 schemes").
+(Sec. 4.1, "Comparison to FLD and M1 schemes").
 
 TEST INFRASTRUCTURE: imported only by the tests and the benchmark's CPU
 baseline; it shares nothing with the product library.

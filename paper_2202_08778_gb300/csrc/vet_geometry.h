@@ -103,7 +103,11 @@ void build_template(const double *d, int ext, int B, double h, unsigned char *ou
   {
     const double w = d[3], x = d[0], y = d[1], z = d[2];
     const double c[10] = {w, w * x, w * y, w * z, w * x * x, w * y * y, w * z * z, w * x * y, w * x * z, w * y * z};
-    for (int m = 0; m < 10; ++m) hd->c[m] = R(c[m]);
+    for (int m = 0; m < 10; ++m) {
+      hd->c[m] = R(c[m]);
+      hd->cp[2 * m] = R(c[m]);
+      hd->cp[2 * m + 1] = (m >= 1 && m <= 3) ? R(-c[m]) : R(c[m]);
+    }
   }
   const TileShape ct = cell_tile(B), nt = node_tile(B);
   const int cstride[3] = {1, ct.sy, ct.sz};  // cell rays walk the cell-pass tile

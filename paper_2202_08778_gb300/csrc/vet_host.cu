@@ -46,6 +46,7 @@ struct vet_ctx {
   long long cell_segs = 0, face_segs = 0;
   int ob[9] = {0};                // octant ranges of the internal direction order
   int face_group = vet::kFaceGroup;  // directions per face-pass item (tunable)
+  unsigned long long tuning_gen = 0;  // bumped whenever the launches change (schedule, tiles)
   cudaStream_t last_stream = nullptr;
   bool timing = false;
   bool timed = false;            // events of the last call were recorded
@@ -137,6 +138,7 @@ vet_status build_schedule(vet_ctx *c, int group) {
   c->level_off = off;
   c->level_group = lg;
   c->face_group = group;
+  ++c->tuning_gen;  // a batch graph captured with the old schedule must not replay
   return VET_OK;
 }
 
@@ -433,10 +435,11 @@ vet_status do_trace(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *I_ou
 }
 
 template <typename R>
-vet_status do_moments(vet_ctx *c, const R *I, R *M_out, void *stream, bool fp64) {
+vet_status do_moments(vet_ctx *c, const R *I, R *M_out, void *stream, bool fp64, double *E64_out = nullptr) {
   vet_status s = check_ctx<R>(c, fp64);
   if (s) return s;
   if (!I || !M_out) return set_err(c, VET_EINVAL, "I and M_out are required");
+  if (E64_out && !is_device_ptr(E64_out)) return set_err(c, VET_EINVAL, "E64_out must be device memory");
   DeviceGuard dg(c->cfg.device);
   if (!dg.ok) return set_err(c, VET_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = (cudaStream_t)stream;
@@ -448,7 +451,8 @@ vet_status do_moments(vet_ctx *c, const R *I, R *M_out, void *stream, bool fp64)
   bool had_host = false;
   s = stage_args<R>(c, st, {{I, (size_t)c->N * nc}}, {{M_out, 10 * nc}}, din, dout, back, bytes, had_host);
   if (s) return s;
-  cudaError_t e = vet::launch_moments<R>(c->dims.ncell, c->N, din[0], (const R *)c->d_coef, dout[0], st);
+  cudaError_t e = vet::launch_moments<R>(c->dims.ncell, c->N, din[0], (const R *)c->d_coef, dout[0], st, E64_out,
+                                         c->dirs_ext[3]);
   if (e) return cuda_err(c, e, "moments launch");
   c->last_stream = st;
   return finish_args<R>(c, st, back, bytes, had_host);
@@ -611,8 +615,8 @@ VET_API vet_status vet_trace(vet_ctx *ctx, const float *kappa, const float *S, c
   return do_trace<float>(ctx, kappa, S, Ib, I_out, stream, false);
 }
 
-VET_API vet_status vet_moments(vet_ctx *ctx, const float *I, float *M_out, void *stream) {
-  return do_moments<float>(ctx, I, M_out, stream, false);
+VET_API vet_status vet_moments(vet_ctx *ctx, const float *I, float *M_out, double *E64_out, void *stream) {
+  return do_moments<float>(ctx, I, M_out, stream, false, E64_out);
 }
 
 VET_API vet_status vet_closure(vet_ctx *ctx, const float *kappa, const float *S, const float *Ib, float *f_out,
@@ -696,7 +700,11 @@ VET_API vet_status vet_set_tuning(vet_ctx *ctx, int face_group, int dir_tile) {
     vet_status st = build_schedule(ctx, face_group);
     if (st != VET_OK) return st;
   }
-  if (dir_tile > 0) ctx->dims.dir_tile = vet::cell_tile_fit(ctx->grid.block, dir_tile, ctx->fp64);
+  if (dir_tile > 0) {
+    const int dt = vet::cell_tile_fit(ctx->grid.block, dir_tile, ctx->fp64);
+    if (dt != ctx->dims.dir_tile) ++ctx->tuning_gen;
+    ctx->dims.dir_tile = dt;
+  }
   return VET_OK;
 }
 
@@ -857,6 +865,9 @@ VET_API vet_status vet_batch_closure(vet_batch *b, const float *const *kappa, co
         (Ib && Ib[i] && !is_device_ptr(Ib[i])) || (M_out && M_out[i] && !is_device_ptr(M_out[i])))
       return batch_err(b, VET_EINVAL, "batch field pointers must be device memory");
     key.insert(key.end(), {kappa[i], S[i], Ib ? Ib[i] : nullptr, f_out[i], M_out ? M_out[i] : nullptr});
+    // a member retuned through vet_batch_context (new schedule or tiles)
+    // invalidates the captured launches
+    key.push_back(reinterpret_cast<const void *>(static_cast<uintptr_t>(b->ctx[i]->tuning_gen)));
   }
   DeviceGuard dg(b->device);
   if (!b->exec || key != b->key) {

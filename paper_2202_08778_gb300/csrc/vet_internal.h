@@ -47,6 +47,11 @@ struct TplHead {
   // nx nz, ny nz) of E, F and P (Eqs. 10-12, c = 1), rounded once from FP64;
   // two unused entries keep the array a multiple of 16 bytes
   alignas(16) R c[12];
+  // the same ten coefficients as pairs (c_m, +-c_m) for a cell and its mirror
+  // cell: the paired cell pass adds I(c, d) + I(c, -d) into E and P and
+  // I(c, d) - I(c, -d) into F, and the mirror cell c' sees -d where c sees d,
+  // so its F pair member is negated
+  alignas(16) R cp[20];
 };
 
 // One event of a ray template: the length of the segment that ends at it,
@@ -179,9 +184,11 @@ template <typename R>
 cudaError_t launch_floor_fix(long long ncell, const R *E, long long E_stride, const void *emax_bits,
                              double floor_rel, R *f_out, cudaStream_t st);
 
+// E64 (optional, device): E of every cell summed in FP64, w64 times the sum
+// of I over the directions (the weights are all equal to w64).
 template <typename R>
 cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef, R *M_out,
-                           cudaStream_t st);
+                           cudaStream_t st, double *E64 = nullptr, double w64 = 0.0);
 
 // Dynamic shared memory of an unpaired face-pass CTA staging `dirs` directions.
 size_t pass_smem_bytes(int B, int dirs, bool fp64);

@@ -16,6 +16,8 @@
 // already in the consumer's upwind frame and padded, so staging is a plain
 // 16-byte copy.  Kernels are compiled for the block edges 8 and 16 (index
 // arithmetic folds to shifts) and for a runtime edge.
+#include <algorithm>
+#include <cstddef>
 #include <cstdint>
 
 #include "vet_internal.h"
@@ -33,25 +35,30 @@ template <typename R> using vec2_t = typename Vec2<R>::T;
 // are stored pre-scaled by -h log2(e)), updates I exactly over a cell of
 // source S: I <- I - (I - S)(1 - e^-x) = S + (I - S) e^-x.  Each form is
 // evaluated where it cannot cancel, as I' = fma(I - S, w, base):
-//   thin (x < 1/2): base = I, w = -(1 - e^-x) = y q(y) with q of degree 4
-//     fitted for relative error by Lawson's iteratively reweighted least
-//     squares (7.7e-8 in exact arithmetic, the level of FP32 rounding): the
-//     other form would round S to its ulp before subtracting almost all of
-//     it when S >> I, and 1 - e would cancel;
-//   thick (x >= 1/2): base = S, w = e^-x from the MUFU (ex2.approx); here
-//     the first form would cancel when I >> S.
-// Thin segments never use the MUFU, whose 1.5e-7 error is not zero-mean and
-// would compound along long thin paths.  FP64: expm1 and exp2 of the CUDA
-// math library in the same two forms.
+//   thin (FP32: x < 1/4): base = I, w = -(1 - e^-x) = y q(y) with q of
+//     degree 3 fitted for relative error by Lawson's iteratively reweighted
+//     least squares (2.4e-7 in exact arithmetic, 3.4e-7 evaluated in FP32):
+//     the other form would round S to its ulp before subtracting almost all
+//     of it when S >> I, and 1 - e would cancel;
+//   thick: base = S, w = e^-x from the MUFU (ex2.approx); here the first
+//     form would cancel when I >> S.  Where S >> I the thick form's result
+//     is about S (1 - e^-x), so the MUFU's relative error (1.5e-7, not
+//     zero-mean) grows by e^-x / (1 - e^-x) <= 3.5 at x >= 1/4.
+// The FMA pipe bounds the FP32 ray march, so the thin range is set to 1/4,
+// where a cubic suffices (a quartic on x < 1/2 costs one more fused
+// multiply-add per segment: 8% of the cell pass).  FP64: expm1 and exp2 of
+// the CUDA math library in the same two forms, thin for x < 1/2.
+constexpr float kQ3 = 8.70478970381660493e-03f, kQ2 = 5.53004379372010468e-02f, kQ1 = 2.40211763951330648e-01f,
+                kQ0 = 6.93147011611337405e-01f;
+constexpr float kThinY = -0.36067376022224085f;  // x < 1/4
 __device__ __forceinline__ float seg_weight(float y, bool &thin) {
   float e;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
-  float q = 1.0833843353054956e-03f;
-  q = fmaf(q, y, 9.4645342235962007e-03f);
-  q = fmaf(q, y, 5.5464640186780434e-02f);
-  q = fmaf(q, y, 2.4022290282685121e-01f);
-  q = fmaf(q, y, 6.9314712699664371e-01f);
-  thin = y > -0.7213475204444817f;  // x < 1/2
+  float q = kQ3;
+  q = fmaf(q, y, kQ2);
+  q = fmaf(q, y, kQ1);
+  q = fmaf(q, y, kQ0);
+  thin = y > kThinY;
   return thin ? q * y : e;
 }
 
@@ -334,11 +341,6 @@ __host__ __device__ inline size_t face_smem_bytes(int B, int nslots) {
   return align16(sizeof(vec2_t<R>) * (size_t)node_tile(B).elems) + (size_t)nslots * face_slot_bytes_t<R>(B);
 }
 
-// ... and of a paired cell-pass CTA (16-byte tile entries).
-__host__ __device__ inline size_t pair_smem_bytes(int B, int nslots) {
-  return align16(sizeof(float4) * (size_t)cell_tile(B).elems) + (size_t)nslots * slot_bytes<float>(B);
-}
-
 constexpr int kDirTile = 4;   // directions per cell-pass tile (two tiles in flight)
 constexpr size_t kSmemMax = 232448 - 64;  // opt-in limit less the static mbarriers
 
@@ -351,16 +353,6 @@ int cell_dir_tile(int B, int want) {
 
 // ---------------------------------------------------------------- face pass
 constexpr int kFaceThreads = 512;
-
-// Directions per tile of the paired cell pass: an even number (whole pairs)
-// whose two buffers fit, at most the tuned tile rounded up to even.
-inline int pair_dir_tile(int B, int want) {
-  int dt = want > 0 ? want : kDirTile;
-  dt = (dt + 1) & ~1;
-  if (dt > kMaxTune) dt = kMaxTune;
-  while (dt > 2 && pair_smem_bytes(B, 2 * dt) > kSmemMax - 4096) dt -= 2;  // 4 KB: the staged order
-  return dt;
-}
 
 // Face pass: one CTA per item (a block and up to kFaceGroup directions of one
 // octant at the same wavefront level).  The CTA loads the block's kappa/S
@@ -658,331 +650,500 @@ __global__ void __launch_bounds__(kCellThreads, 2)
 // negation (HEALPix sets are, rotated or not).  The ray from cell c in
 // direction d and the ray from the point-mirrored cell c' = (B-1-x, B-1-y,
 // B-1-z) in direction -d are mirror images (and so are (c, -d) and (c', d)):
-// in their own upwind frames both
-// start at the same coordinates along every axis the direction crosses, leave
-// through the same event with the same exit-table entries, and cross segments
-// of the same lengths whose tile offsets are negatives of each other.  So one
-// thread marches both in lockstep from one event list and one 16-byte load
-// of the paired tile per step, with the two exponentials' arithmetic on
-// packed FP32 pairs (f32x2); only the in-plane face coordinates (which may
-// differ along an axis the direction does not cross) and the staged faces
-// are per ray.  The lanes of a warp march aligned at the downwind end, as in
-// the face pass, so that at each step they read one event and a brick of
-// neighbouring entries.  The cell order lists the pairs (d, -d)
-// consecutively; a staged tile holds dt / 2 pairs.
-// one lower-half cell and its mirror per thread; 512 threads (two CTAs per SM)
-// for 16^3 blocks, where three 256-thread CTAs would hold fewer warps
-__host__ __device__ constexpr int pair_threads(int B) { return B == 16 ? 512 : 256; }
+// in their own upwind frames both start at the same coordinates along every
+// axis the direction crosses, leave through the same event with the same
+// exit-table entries, and cross segments of the same lengths whose tile
+// offsets are negatives of each other.  So one thread marches both in
+// lockstep from one event list and one 16-byte load of the paired tile per
+// step, with the two exponentials' arithmetic on packed FP32 pairs (f32x2);
+// only the staged faces (and, along an axis the direction does not cross,
+// the in-plane face coordinates) are per ray.  The lanes of a warp march
+// aligned at the downwind end, as in the face pass, so that at each step they
+// read one event and a brick of neighbouring entries.  The cell order lists
+// the pairs (d, -d) consecutively; every staged tile holds whole pairs.
+//
+// Each thread owns one cell of the block's lower half and its mirror: for
+// 16^3 blocks 1024 threads (one CTA per SM, whose 32 warps share one kappa/S
+// tile and a deep ring of staged directions), for 8^3 blocks 256.  All
+// shared-memory addressing is 32-bit (the state of a march is a handful of
+// registers: the pair's intensities, the tile address of the start entries
+// and the event index, which is the same for the whole warp).
+__host__ __device__ constexpr int pair_threads(int B) { return B == 16 ? 1024 : 256; }
+__host__ __device__ constexpr int pair_min_ctas(int B) { return B == 16 ? 1 : 4; }
+constexpr int kPairStagesMax = 16;  // staging ring depth limit of the paired cell pass
 
-__device__ __forceinline__ uint64_t pk2(float a, float b) {
-  return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
+// Shared-memory loads at 32-bit shared-window addresses.  volatile keeps
+// them after the mbarrier waits that publish the staged data.
+__device__ __forceinline__ uint4 lds_4x32(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
 }
-__device__ __forceinline__ void upk2(uint64_t r, float &a, float &b) {
-  a = __uint_as_float((uint32_t)r);
-  b = __uint_as_float((uint32_t)(r >> 32));
+__device__ __forceinline__ uint2 lds_2x32(uint32_t a) {
+  uint2 v;
+  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
 }
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
 }
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
+__device__ __forceinline__ int lds_s16(uint32_t a) {
+  int v;
+  asm volatile("ld.shared.s16 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
 }
 
-// The paired tiles of both mirrored passes hold 16-byte entries (kappa(p),
-// kappa(p'), S(p), S(p')): p' is the cell where the mirror ray stands when
-// the primary ray stands at p.  Template offsets are for 8-byte entries,
-// hence 2 * off below.
 
-// One ray on a paired tile, on a template of its own (a pair whose templates
-// are not exact mirrors): march() reading the ray's own (kappa, S) = (.x, .z).
-__device__ __forceinline__ float march4(const unsigned char *__restrict__ tb, int last,
-                                       const TplEvent<float> *__restrict__ ev, float I) {
-  for (int e = last; e >= 0; --e) {
-    const TplEvent<float> E = ev[e];
-    const float4 q = *reinterpret_cast<const float4 *>(tb + 2 * E.off);
-    bool thin;
-    const float w = seg_weight(q.x * E.len, thin);
-    I = fmaf(I - q.z, w, thin ? I : q.z);
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+// One segment of both rays of a mirrored pair (the update of segment() on
+// packed FP32 pairs, f32x2).  ta: shared address of the paired tile entry
+// (kappa, kappa', S, S') the primary ray crosses; len: the segment's scaled
+// length.  Both forms are formed and each lane keeps the one that cannot
+// cancel: thin  I + (I - S) * (-(1 - e^-x)),  thick  S + (I - S) e^-x.
+__device__ __forceinline__ float2 step_pair(uint32_t ta, float len, float2 I) {
+  const float4 q = lds_f4(ta);
+  const float2 Y = __fmul2_rn(make_float2(q.x, q.y), make_float2(len, len));
+  float e1, e2;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(Y.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(Y.y));
+  float2 p = __ffma2_rn(make_float2(kQ3, kQ3), Y, make_float2(kQ2, kQ2));
+  p = __ffma2_rn(p, Y, make_float2(kQ1, kQ1));
+  p = __ffma2_rn(p, Y, make_float2(kQ0, kQ0));
+  const float2 n = __fmul2_rn(p, Y);
+  const bool t1 = Y.x > kThinY, t2 = Y.y > kThinY;
+  // one FFMA2 on per-lane selected operands: the FMA pipe, not issue, bounds
+  // this step (an FFMA2 of each form and a select of the results measured
+  // 13% slower)
+  return __ffma2_rn(__fadd2_rn(I, neg2(make_float2(q.z, q.w))), make_float2(t1 ? n.x : e1, t2 ? n.y : e2),
+                    make_float2(t1 ? I.x : q.z, t2 ? I.y : q.w));
+}
+
+// March of a mirrored ray pair: events at shared address ev (8 bytes each:
+// scaled length, byte offset for 8-byte tile entries), primary start entry
+// at t1.  The warp runs from its largest `last` down to event 0; a lane
+// whose own ray is shorter reads the identity entry id (kappa = 0: the thin
+// form returns I exactly) until the index reaches its `last`; below the
+// warp's smallest `last` every lane marches and events are read in 16-byte
+// pairs.
+__device__ __forceinline__ float2 march_pair(uint32_t t1, uint32_t id, uint32_t ev, int last, float2 I) {
+  int e = __reduce_max_sync(0xffffffffu, last);
+  const int wmin = __reduce_min_sync(0xffffffffu, last);
+  for (; e > wmin; --e) {
+    const float2 v = lds_f2(ev + 8 * e);
+    I = step_pair(e <= last ? t1 + 2 * (int)__float_as_uint(v.y) : id, v.x, I);
+  }
+  if (e >= 0 && !(e & 1)) {  // to an odd index: event pairs (e - 1, e) are 16-byte aligned
+    const float2 v = lds_f2(ev + 8 * e);
+    I = step_pair(t1 + 2 * (int)__float_as_uint(v.y), v.x, I);
+    --e;
+  }
+  for (; e >= 3; e -= 4) {
+    const float4 a = lds_f4(ev + 8 * (e - 1));
+    const float4 b = lds_f4(ev + 8 * (e - 3));
+    I = step_pair(t1 + 2 * (int)__float_as_uint(a.w), a.z, I);
+    I = step_pair(t1 + 2 * (int)__float_as_uint(a.y), a.x, I);
+    I = step_pair(t1 + 2 * (int)__float_as_uint(b.w), b.z, I);
+    I = step_pair(t1 + 2 * (int)__float_as_uint(b.y), b.x, I);
+  }
+  if (e == 1) {
+    const float4 a = lds_f4(ev);
+    I = step_pair(t1 + 2 * (int)__float_as_uint(a.w), a.z, I);
+    I = step_pair(t1 + 2 * (int)__float_as_uint(a.y), a.x, I);
   }
   return I;
 }
 
-// One cell ray on its own template (upwind-frame coordinates l0..l2, start
-// entry at byte address tb of the paired tile): exit lookup, entry value,
-// march.
-__device__ __forceinline__ float cell_ray4(const Tpl<float> &T, const float *fin, int fstride, int B, int l0, int l1,
-                                           int l2, const unsigned char *tb) {
-  const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
-  int last = p0, ae = 0, la = l0, lb = l1, lc = l2;
-  if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; }
-  if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; }
-  const int row = (ae * 2) * B + la;
-  const float Iin = face_value<float>(fin, fstride, B, ae, lb, lc, T.ck[row], T.ck[row + B], T.cw[row], T.cw[row + B]);
-  return march4(tb, last, T.cev, Iin);
+// One ray on its own template (a pair whose templates are not exact
+// mirrors), reading its own (kappa, S) = (.x, .z) of the paired entries.
+__device__ __forceinline__ float march_one(uint32_t t, uint32_t ev, int last, float I) {
+  for (int e = last; e >= 0; --e) {
+    const uint2 v = lds_2x32(ev + 8 * e);
+    const uint4 q = lds_4x32(t + 2 * (int)v.y);
+    const float y = __uint_as_float(q.x) * __uint_as_float(v.x);
+    float ex;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(y));
+    float p = kQ3;
+    p = fmaf(p, y, kQ2);
+    p = fmaf(p, y, kQ1);
+    p = fmaf(p, y, kQ0);
+    const float s = __uint_as_float(q.z), D = I - s;
+    I = y > kThinY ? fmaf(D, p * y, I) : fmaf(D, ex, s);
+  }
+  return I;
 }
 
-// Paired tile of the cell pass: p' is the point-mirrored cell of the same
-// block.  (Issuing all loads before the stores, as the face passes do, made
-// this kernel slower.)
-template <int BC>
-__device__ __forceinline__ void load_tile_pair(float4 *tile, TileShape ts, const GridDims &g, int bx, int by, int bz,
-                                               const float *__restrict__ kappa, const float *__restrict__ S) {
-  constexpr int B = BC, B2 = B * B, B3 = B2 * B;
-  for (int i = threadIdx.x; i < B3; i += blockDim.x) {
-    const int x = i % B, y = (i / B) % B, z = i / B2;
-    const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
-    const long long gm = ((long long)(bz * B + B - 1 - z) * g.ny + (by * B + B - 1 - y)) * g.nx + (bx * B + B - 1 - x);
-    tile[x + ts.sy * y + ts.sz * z] = make_float4(kappa[gi], kappa[gm], S[gi], S[gm]);
+// Paired-cell-pass slot: the template head, the template's cell-ray parts,
+// then the three incoming faces (offsets in bytes from the slot's start).
+struct CellSlot {
+  int cev, cpos, ck, cw, faces, bytes;
+};
+__host__ __device__ inline CellSlot cell_slot(int B) {
+  const TplLayout L = tpl_layout<float>(B);
+  const int shift = L.cev - L.nev;  // the node-ray parts are not staged
+  CellSlot s;
+  s.cev = L.cev - shift;
+  s.cpos = L.cpos - shift;
+  s.ck = L.ck - shift;
+  s.cw = L.cw - shift;
+  s.faces = L.bytes - shift;
+  s.bytes = s.faces + (int)faces_bytes<float>(B);
+  return s;
+}
+
+// Issues the bulk copies of one paired-cell-pass slot (thread 0): the
+// head, the cell-ray parts and the three incoming faces of direction d.
+__device__ __forceinline__ void issue_cell_slot(unsigned char *slot, const GridDims &g, const TplLayout &TL,
+                                                const CellSlot &CS, int bx, int by, int bz, int d, int sgn_bits,
+                                                const unsigned char *__restrict__ tpl_g, const float *__restrict__ faces,
+                                                const float *__restrict__ bnd, uint64_t *bar) {
+  const unsigned char *src = tpl_g + (size_t)d * TL.bytes;
+  bulk_g2s(slot, src, (uint32_t)TL.nev, bar);
+  bulk_g2s(slot + CS.cev, src + TL.cev, (uint32_t)(TL.bytes - TL.cev), bar);
+  const int nblk = g.nbx * g.nby * g.nbz;
+  const uint32_t fb = (uint32_t)(g.fstride * sizeof(float));
+  const int b3[3] = {bx, by, bz};
+  const int nb3[3] = {g.nbx, g.nby, g.nbz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int s = (sgn_bits >> a) & 1 ? -1 : 1;
+    int nb[3] = {b3[0], b3[1], b3[2]};
+    nb[a] -= s;
+    const float *fsrc;
+    if (nb[a] < 0 || nb[a] >= nb3[a]) {
+      fsrc = bnd + ((long long)(2 * a + (s > 0 ? 0 : 1)) * g.ndir + d) * g.fstride;
+    } else {
+      const long long nid = ((long long)nb[2] * g.nby + nb[1]) * g.nbx + nb[0];
+      fsrc = faces + (((long long)d * nblk + nid) * 3 + a) * g.fstride;
+    }
+    bulk_g2s(slot + CS.faces + a * fb, fsrc, fb, bar);
   }
 }
 
-// One segment of both rays of a mirrored pair on a paired tile (tb: the
-// primary ray's start entry): the update and the two forms of segment() on
-// packed FP32 pairs.
-__device__ __forceinline__ void segment_pair_tile(const unsigned char *__restrict__ tb, const TplEvent<float> &ev,
-                                                  uint64_t &I) {
-  const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(tb + 2 * ev.off);  // (k, k'), (S, S')
-  const uint64_t Y = mul2(q.x, pk2(ev.len, ev.len));
-  float y1, y2;
-  upk2(Y, y1, y2);
-  float e1, e2;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(y1));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(y2));
-  uint64_t p = pk2(1.0833843353054956e-03f, 1.0833843353054956e-03f);
-  p = fma2(p, Y, pk2(9.4645342235962007e-03f, 9.4645342235962007e-03f));
-  p = fma2(p, Y, pk2(5.5464640186780434e-02f, 5.5464640186780434e-02f));
-  p = fma2(p, Y, pk2(2.4022290282685121e-01f, 2.4022290282685121e-01f));
-  p = fma2(p, Y, pk2(6.9314712699664371e-01f, 6.9314712699664371e-01f));
-  float n1, n2;  // -(1 - e^-x) of the thin form
-  upk2(mul2(p, Y), n1, n2);
-  const bool thin1 = y1 > -0.7213475204444817f, thin2 = y2 > -0.7213475204444817f;
-  float i1, i2, s1, s2;
-  upk2(I, i1, i2);
-  upk2(q.y, s1, s2);
-  I = fma2(sub2(I, q.y), pk2(thin1 ? n1 : e1, thin2 ? n2 : e2), pk2(thin1 ? i1 : s1, thin2 ? i2 : s2));
+// Non-blocking test of a phase (no suspension).
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
 }
 
+// One potentially blocking poll: the hardware may suspend the thread for a
+// short while when the phase is not complete.
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait of one thread: a test, then up to limit - 1 blocking polls,
+// four per trip of a 32-bit counter, so that a waiting warp spends few issue
+// slots on the loop itself (a loop of 64-bit counters, a sleep schedule and
+// single polls took a third of the cell pass's issued instructions).
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t a, uint32_t parity, long long limit) {
+  if (limit < 1) return false;
+  if (mbar_test(a, parity)) return true;
+  int n = limit - 1 > 0x7ffffff0LL ? 0x7ffffff0 : (int)(limit - 1);
+  for (; n >= 4; n -= 4)
+    if (mbar_try(a, parity) || mbar_try(a, parity) || mbar_try(a, parity) || mbar_try(a, parity)) return true;
+  for (; n > 0; --n)
+    if (mbar_try(a, parity)) return true;
+  return false;
+}
+
+// The same wait taken by every lane of a converged warp, with a warp-wide
+// verdict (the warp proceeds only if every lane saw the phase complete).
+__device__ __forceinline__ bool mbar_wait_sleep_warp(uint32_t a, uint32_t parity, long long limit, int *status,
+                                                     int code) {
+  const bool done = mbar_wait_sleep(a, parity, limit);
+  if (__all_sync(0xffffffffu, done)) return true;
+  if ((threadIdx.x & 31) == 0) atomicOr(status, code);
+  return false;
+}
+
+// Dynamic shared memory of a paired cell-pass CTA: the paired tile and
+// `nslots` staged directions.
+__host__ __device__ inline size_t pair_smem_bytes(int B, int nslots) {
+  return align16(sizeof(float4) * (size_t)cell_tile(B).elems) + (size_t)nslots * cell_slot(B).bytes;
+}
+
+// Paired tile of the cell pass: entry p holds (kappa(p), kappa(p'), S(p),
+// S(p')), p' the point-mirrored cell of the same block; every thread issues
+// its global loads before its stores.
+template <int BC, int NT>
+__device__ __forceinline__ void load_tile_pair(float4 *tile, TileShape ts, const GridDims &g, int bx, int by, int bz,
+                                               const float *__restrict__ kappa, const float *__restrict__ S) {
+  constexpr int B = BC, B2 = B * B, K = B2 * B / NT;
+  static_assert(B2 * B % NT == 0, "tile cells must divide evenly over the threads");
+  float4 v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int i = (int)threadIdx.x + k * NT, x = i % B, y = (i / B) % B, z = i / B2;
+    const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
+    const long long gm = ((long long)(bz * B + B - 1 - z) * g.ny + (by * B + B - 1 - y)) * g.nx + (bx * B + B - 1 - x);
+    v[k] = make_float4(kappa[gi], kappa[gm], S[gi], S[gm]);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int i = (int)threadIdx.x + k * NT, x = i % B, y = (i / B) % B, z = i / B2;
+    tile[x + ts.sy * y + ts.sz * z] = v[k];
+  }
+}
+
+// Compensated (Kahan) accumulation of t = c * x into s on packed pairs; nc
+// holds the negated compensation.
+__device__ __forceinline__ void kahan2(float2 &s, float2 &nc, float2 c, float2 x) {
+  const float2 y = __ffma2_rn(c, x, nc);
+  const float2 t = __fadd2_rn(s, y);
+  nc = __fadd2_rn(y, neg2(__fadd2_rn(t, neg2(s))));
+  s = t;
+}
+
+// the head fields the paired cell pass reads at fixed offsets
+static_assert(offsetof(TplHead<float>, sgn) == 16 && offsetof(TplHead<float>, ext) == 28 &&
+                  offsetof(TplHead<float>, mirror) == 32 && offsetof(TplHead<float>, cp) % 16 == 0,
+              "TplHead<float> layout");
+
 template <int MODE, int BC>
-__global__ void __launch_bounds__(pair_threads(BC), BC == 16 ? 2 : 3)
-    cell_pair_kernel(GridDims g, int parts, int dt, const float *__restrict__ kappa, const float *__restrict__ S,
-                     const unsigned char *__restrict__ tpl_g, const int *__restrict__ order,
-                     const float *__restrict__ faces, const float *__restrict__ bnd, float *__restrict__ I_out,
-                     float *__restrict__ M_out, float *__restrict__ E_out, float *__restrict__ f_out, void *emax_bits,
-                     long long spin_limit, int *status, const int *__restrict__ block_list) {
-  constexpr int B = BC, B2 = B * B;
+__global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
+    cell_pair_kernel(GridDims g, int parts, int dt, int nstage, const float *__restrict__ kappa,
+                     const float *__restrict__ S, const unsigned char *__restrict__ tpl_g,
+                     const int *__restrict__ order, const float *__restrict__ faces, const float *__restrict__ bnd,
+                     float *__restrict__ I_out, float *__restrict__ M_out, float *__restrict__ E_out,
+                     float *__restrict__ f_out, void *emax_bits, long long spin_limit, int *status,
+                     const int *__restrict__ block_list) {
+  constexpr int B = BC, B2 = B * B, NT = pair_threads(BC);
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[2], empty[2];
+  __shared__ __align__(8) uint64_t full[kPairStagesMax], empty[kPairStagesMax];
   constexpr int kOrdMax = 1024;  // direction sets up to nside = 8 keep their order in shared memory
   __shared__ int s_ord[kOrdMax];
   const bool ord_smem = g.ndir <= kOrdMax;
   const TileShape ts = cell_tile(B);
   const TplLayout TL = tpl_layout<float>(B);
+  const CellSlot CS = cell_slot(B);
   const int fstride = g.fstride;
-  const size_t sb = slot_bytes<float>(B);
   float4 *tile = reinterpret_cast<float4 *>(smem);
-  unsigned char *buf0 = smem + align16(sizeof(float4) * (size_t)ts.elems);
+  unsigned char *ring = smem + align16(sizeof(float4) * (size_t)ts.elems);
+  const uint32_t ring_s = smem_u32(ring);
+  const size_t stage_bytes = (size_t)dt * CS.bytes;
   const int item = blockIdx.x / parts, part = blockIdx.x - item * parts;
   const int blk = block_list ? block_list[item] : item;
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
-  const int nwarps = blockDim.x >> 5;
+  constexpr int nwarps = NT / 32;
   const int ntiles = (g.ndir + dt - 1) / dt;
+  // producer state, meaningful in thread 0 only
   int issued = 0, consumed = 0;
-  auto issue_tile = [&](int t) {  // thread 0 only
-    issued = t + 1;
-    const int b = t & 1, d0 = t * dt, nd = min(dt, g.ndir - d0);
-    unsigned char *buf = buf0 + (size_t)b * dt * sb;
-    mbar_expect_tx(&full[b], (uint32_t)(sb * nd));
+  auto issue_tile = [&](int t) {
+    const int s = t % nstage, d0 = t * dt, nd = min(dt, g.ndir - d0);
+    unsigned char *buf = ring + (size_t)s * stage_bytes;
+    mbar_expect_tx(&full[s], (uint32_t)(CS.bytes * nd));
     for (int j = 0; j < nd; ++j) {
-      const int v = (ord_smem && t >= 2) ? s_ord[d0 + j] : order[d0 + j];
-      issue_slot<float>(buf + sb * j, g, TL, bx, by, bz, order_dir(v), tpl_g, faces, bnd, &full[b], TL.bytes,
-                        order_sgn(v));
+      const int v = (ord_smem && t >= nstage) ? s_ord[d0 + j] : order[d0 + j];
+      issue_cell_slot(buf + (size_t)CS.bytes * j, g, TL, CS, bx, by, bz, order_dir(v), (v >> 16) & 7, tpl_g, faces,
+                      bnd, &full[s]);
     }
   };
   if (threadIdx.x == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&empty[0], nwarps);
-    mbar_init(&empty[1], nwarps);
+    for (int s = 0; s < nstage; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], nwarps);
+    }
     mbar_fence_init();
     griddep_wait();  // the faces are the face pass's output
-    issue_tile(0);
-    if (ntiles > 1) issue_tile(1);
+    while (issued < ntiles && issued < nstage) issue_tile(issued++);
   }
   if (ord_smem)
-    for (int i = threadIdx.x; i < g.ndir; i += blockDim.x) s_ord[i] = order[i];
-  load_tile_pair<BC>(tile, ts, g, bx, by, bz, kappa, S);
+    for (int i = threadIdx.x; i < g.ndir; i += NT) s_ord[i] = order[i];
+  load_tile_pair<BC, NT>(tile, ts, g, bx, by, bz, kappa, S);
+  if (threadIdx.x == 0) tile[B] = make_float4(0.f, 0.f, 0.f, 0.f);  // identity entry (padding, x = B)
   __syncthreads();
 
   // this thread's lower-half cell (z < B/2): 4 x 4 x 2 bricks, warp-major
-  const int q = part * pair_threads(BC) + (int)threadIdx.x;
+  const int q = part * NT + (int)threadIdx.x;
   const int qb = q >> 5, ln = q & 31;
   const int cx = 4 * (qb % (B / 4)) + (ln & 3);
   const int cy = 4 * ((qb / (B / 4)) % (B / 4)) + ((ln >> 2) & 3);
   const int cz = 2 * (qb / (B2 / 16)) + (ln >> 4);
   const int mx = B - 1 - cx, my = B - 1 - cy, mz = B - 1 - cz;  // the mirror cell
-  const unsigned char *t1 = reinterpret_cast<const unsigned char *>(tile + (cx + ts.sy * cy + ts.sz * cz));
-  const unsigned char *t2 = reinterpret_cast<const unsigned char *>(tile + (mx + ts.sy * my + ts.sz * mz));
+  const uint32_t tile_s = smem_u32(tile);
+  const uint32_t t1 = tile_s + 16u * (uint32_t)(cx + ts.sy * cy + ts.sz * cz);
+  const uint32_t t2 = tile_s + 16u * (uint32_t)(mx + ts.sy * my + ts.sz * mz);
   const long long gc1 = ((long long)(bz * B + cz) * g.ny + (by * B + cy)) * g.nx + (bx * B + cx);
   const long long gc2 = ((long long)(bz * B + mz) * g.ny + (by * B + my)) * g.nx + (bx * B + mx);
   constexpr bool kWantF = MODE == 0;
-  float mom[2][10], cmp[2][4];
+  // moments of (c, c') as packed pairs: E, Fx, Fy, Fz, Pxx, Pyy, Pzz, Pxy,
+  // Pxz, Pyz; compensated E and Pii (nc: their negated compensations)
+  float2 mom[10], nc[4];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+  for (int m = 0; m < 10; ++m) mom[m] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int m = 0; m < 10; ++m) mom[r][m] = 0.f;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) cmp[r][m] = 0.f;
-  }
+  for (int m = 0; m < 4; ++m) nc[m] = make_float2(0.f, 0.f);
+  // a tile padding entry (x = B) set to zero: the identity segment
+  const uint32_t id_s = tile_s + 16u * (uint32_t)B;
+  constexpr int W = B + 2;
+  const uint32_t fW = 4u * W;
 
-  // plain FP32 partial sums over four tiles, folded into the compensated
-  // sums after the fourth (or the last) tile
-  float part_[2][10];
-#pragma unroll
-  for (int r = 0; r < 2; ++r)
-#pragma unroll
-    for (int m = 0; m < 10; ++m) part_[r][m] = 0.f;
+  // Exit lookup and entry value of the ray(s) of one march: primary slot ps
+  // (its template), upwind-frame coordinates l0..l2; returns the pair of
+  // entry intensities from faces f1 (primary) and f2 (the pair's second ray).
+  auto entry = [&](uint32_t ps, int l0, int l1, int l2, uint32_t f1, uint32_t f2, int &last) -> float2 {
+    const int p0 = lds_s16(ps + CS.cpos + 2 * l0), p1 = lds_s16(ps + CS.cpos + 2 * (B + l1)),
+              p2 = lds_s16(ps + CS.cpos + 2 * (2 * B + l2));
+    int ae = 0, la = l0, lb = l1, lc = l2;
+    last = p0;
+    if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; }
+    if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; }
+    const int row = (ae * 2) * B + la;
+    const int kb = lds_s16(ps + CS.ck + 2 * row), kc = lds_s16(ps + CS.ck + 2 * (row + B));
+    const uint2 ub = lds_2x32(ps + CS.cw + 8 * row), uc = lds_2x32(ps + CS.cw + 8 * (row + B));
+    const float wbx = __uint_as_float(ub.x), wby = __uint_as_float(ub.y);
+    const float wcx = __uint_as_float(uc.x), wcy = __uint_as_float(uc.y);
+    const int ib = max(lb + kb, 0), ic = max(lc + kc, 0);
+    const uint32_t fo = 4u * (uint32_t)(ae * fstride + ib * W + ic);
+    const uint32_t a1 = f1 + fo, a2 = f2 + fo;
+    const float I1 = wby * (wcy * lds_f32(a1) + wcx * lds_f32(a1 + 4)) +
+                     wbx * (wcy * lds_f32(a1 + fW) + wcx * lds_f32(a1 + fW + 4));
+    const float I2 = wby * (wcy * lds_f32(a2) + wcx * lds_f32(a2 + 4)) +
+                     wbx * (wcy * lds_f32(a2 + fW) + wcx * lds_f32(a2 + fW + 4));
+    return make_float2(I1, I2);
+  };
+  // one ray of a pair that is not an exact mirror image: its own template
+  // (slot ps, signs sg), start cell (x, y, z), entry face f
+  auto single = [&](uint32_t ps, uint4 hd, int x, int y, int z, uint32_t tstart) -> float {
+    const int l0 = (int)hd.x > 0 ? x : B - 1 - x;
+    const int l1 = (int)hd.y > 0 ? y : B - 1 - y;
+    const int l2 = (int)hd.z > 0 ? z : B - 1 - z;
+    int last;
+    const float2 Iin = entry(ps, l0, l1, l2, ps + CS.faces, ps + CS.faces, last);
+    return march_one(tstart, ps + CS.cev, last, Iin.x);
+  };
+
   bool ok = true;
+  const uint32_t full_s = smem_u32(full), empty_s = smem_u32(empty);
   for (int t = 0; t < ntiles && ok; ++t) {
-    const int b = t & 1;
-    const uint32_t ph = (uint32_t)((t >> 1) & 1);
-    if (!mbar_wait_warp(&full[b], ph, spin_limit, status, 2)) { ok = false; break; }
-    consumed = t + 1;
+    const int st = t % nstage;
+    const uint32_t ph = (uint32_t)((t / nstage) & 1);
+    if (threadIdx.x < 32) {  // warp 0: thread 0 makes sure tile t is in flight
+      int pok = 1;
+      if (threadIdx.x == 0) {
+        // its stage must have been released by every warp for tile t - nstage
+        while (pok && issued <= t) {
+          pok = mbar_wait_sleep(empty_s + 8 * (issued % nstage), (uint32_t)(((issued / nstage) - 1) & 1),
+                                spin_limit);
+          if (pok) issue_tile(issued++);
+          else atomicOr(status, 4);
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, pok, 0)) { ok = false; break; }
+    }
+    if (!mbar_wait_sleep_warp(full_s + 8 * st, ph, spin_limit, status, 2)) { ok = false; break; }
+    if (threadIdx.x == 0) consumed = t + 1;
     const int nd = min(dt, g.ndir - t * dt);
-    const unsigned char *buf = buf0 + (size_t)b * dt * sb;
-    // every cell needs both members of a pair: (c, d) with (c', -d), then
-    // (c, -d) with (c', d), the primary direction's template driving each
-    for (int jj = 0; jj < nd; ++jj) {
-      const int j = (jj >> 1) << 1, j1 = j + (jj & 1), j2 = j + 1 - (jj & 1);
-      const Tpl<float> T(buf + sb * j1, TL);  // primary: events and tables
-      const TplHead<float> *H2 = reinterpret_cast<const TplHead<float> *>(buf + sb * j2);  // its antipode
-      const float *fin1 = reinterpret_cast<const float *>(buf + sb * j1 + TL.bytes);
-      const float *fin2 = reinterpret_cast<const float *>(buf + sb * j2 + TL.bytes);
-      // upwind-frame coordinates of the cell in d; on a mirrored pair (every
-      // sign flips) the mirror cell in -d has the same ones, since each
-      // coordinate c becomes B - 1 - c, so both rays share them, their exit
-      // and their face index
-      const int l0 = T.h->sgn[0] > 0 ? cx : B - 1 - cx;
-      const int l1 = T.h->sgn[1] > 0 ? cy : B - 1 - cy;
-      const int l2 = T.h->sgn[2] > 0 ? cz : B - 1 - cz;
-      float I1, I2;
-      if (T.h->mirror) {
-        const int p0 = T.cpos[l0], p1 = T.cpos[B + l1], p2 = T.cpos[2 * B + l2];
-        int last = p0, ae = 0, la = l0, lb = l1, lc = l2;
-        if (p1 < last) { last = p1; ae = 1; la = l1; lb = l0; }
-        if (p2 < last) { last = p2; ae = 2; la = l2; lb = l0; lc = l1; }
-        const int row = (ae * 2) * B + la;
-        const int kb = T.ck[row], kc = T.ck[row + B];
-        const float2 wb = T.cw[row], wc = T.cw[row + B];
-        const float Iin1 = face_value<float>(fin1, fstride, B, ae, lb, lc, kb, kc, wb, wc);
-        const float Iin2 = face_value<float>(fin2, fstride, B, ae, lb, lc, kb, kc, wb, wc);
-        uint64_t I = pk2(Iin1, Iin2);
-        // aligned at the downwind end; once the event index reaches the
-        // warp's smallest `last` every lane marches and the identity
-        // selects are dropped (the face passes, whose warps more often mix
-        // templates and upwind-face nodes, measured slower with this split)
-        int e = __reduce_max_sync(0xffffffffu, last);
-        const int wmin = __reduce_min_sync(0xffffffffu, last);
-        for (; e - 1 > wmin; e -= 2) {  // some lanes not yet started
-          TplEvent<float> e0 = T.cev[e], e1 = T.cev[e - 1];
-          if (e > last) { e0.len = 0.f; e0.off = 0; }
-          if (e - 1 > last) { e1.len = 0.f; e1.off = 0; }
-          segment_pair_tile(t1, e0, I);
-          segment_pair_tile(t1, e1, I);
+    const uint32_t buf = ring_s + (uint32_t)(st * stage_bytes);
+    for (int j = 0; j < nd; j += 2) {  // the antipodal pair (j, j + 1)
+      const uint32_t sa = buf + (uint32_t)(CS.bytes * j), sb = sa + (uint32_t)CS.bytes;
+      const uint4 ha = lds_4x32(sa + 16), hb = lds_4x32(sb + 16);  // (sgn0, sgn1, sgn2, ext)
+      const int mirror = (int)lds_2x32(sa + 32).x;
+      float2 m1, m2;  // m1 = (I(c, d), I(c', -d)), m2 = (I(c, -d), I(c', d))
+      if (mirror) {
+        // upwind-frame coordinates of c in the primary direction; the mirror
+        // cell in the antipode has the same ones (each flips to B - 1 - c)
+        int last;
+        {
+          const int l0 = (int)ha.x > 0 ? cx : mx, l1 = (int)ha.y > 0 ? cy : my, l2 = (int)ha.z > 0 ? cz : mz;
+          const float2 Iin = entry(sa, l0, l1, l2, sa + CS.faces, sb + CS.faces, last);
+          m1 = march_pair(t1, id_s, sa + CS.cev, last, Iin);
         }
-        if (e > wmin) {
-          TplEvent<float> e0 = T.cev[e];
-          if (e > last) { e0.len = 0.f; e0.off = 0; }
-          segment_pair_tile(t1, e0, I);
-          --e;
+        {
+          const int l0 = (int)hb.x > 0 ? cx : mx, l1 = (int)hb.y > 0 ? cy : my, l2 = (int)hb.z > 0 ? cz : mz;
+          const float2 Iin = entry(sb, l0, l1, l2, sb + CS.faces, sa + CS.faces, last);
+          m2 = march_pair(t1, id_s, sb + CS.cev, last, Iin);
         }
-        for (; e > 0; e -= 2) {  // every lane marching
-          segment_pair_tile(t1, T.cev[e], I);
-          segment_pair_tile(t1, T.cev[e - 1], I);
-        }
-        if (e == 0) segment_pair_tile(t1, T.cev[0], I);
-        upk2(I, I1, I2);
       } else {
         // the pair's templates differ (near-tied plane crossings ordered
         // differently): each ray follows its own direction's template
-        const Tpl<float> T2(buf + sb * j2, TL);
-        I1 = cell_ray4(T, fin1, fstride, B, l0, l1, l2, t1);
-        const int m0 = H2->sgn[0] > 0 ? mx : B - 1 - mx;
-        const int m1 = H2->sgn[1] > 0 ? my : B - 1 - my;
-        const int m2 = H2->sgn[2] > 0 ? mz : B - 1 - mz;
-        I2 = cell_ray4(T2, fin2, fstride, B, m0, m1, m2, t2);
+        m1 = make_float2(single(sa, ha, cx, cy, cz, t1), single(sb, hb, mx, my, mz, t2));
+        m2 = make_float2(single(sb, hb, cx, cy, cz, t1), single(sa, ha, mx, my, mz, t2));
       }
       if (MODE == 1) {
-        I_out[(long long)T.h->ext * g.ncell + gc1] = I1;
-        I_out[(long long)H2->ext * g.ncell + gc2] = I2;
+        I_out[(long long)ha.w * g.ncell + gc1] = m1.x;
+        I_out[(long long)hb.w * g.ncell + gc2] = m1.y;
+        I_out[(long long)hb.w * g.ncell + gc1] = m2.x;
+        I_out[(long long)ha.w * g.ncell + gc2] = m2.y;
       } else {
-        const float *c1 = T.h->c, *c2 = H2->c;
-#pragma unroll
-        for (int m = 0; m < 10; ++m)
-          if (kWantF || m == 0 || m >= 4) {
-            part_[0][m] = fmaf(I1, c1[m], part_[0][m]);
-            part_[1][m] = fmaf(I2, c2[m], part_[1][m]);
-          }
-      }
-    }
-    if (MODE != 1 && ((t & 3) == 3 || t + 1 == ntiles)) {
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {  // E, Pxx, Pyy, Pzz: compensated fold
-          const int m = qq == 0 ? 0 : 3 + qq;
-          const float y = part_[r][m] - cmp[r][qq];
-          const float tt = mom[r][m] + y;
-          cmp[r][qq] = (tt - mom[r][m]) - y;
-          mom[r][m] = tt;
-        }
+        // E and P take I(d) + I(-d), F takes I(d) - I(-d), with the primary
+        // direction's coefficient pairs
+        const float2 sum = __fadd2_rn(m1, m2), dif = __fadd2_rn(m1, neg2(m2));
+        const uint32_t cpa = sa + (uint32_t)offsetof(TplHead<float>, cp);
+        const float4 c01 = lds_f4(cpa), c23 = lds_f4(cpa + 16), c45 = lds_f4(cpa + 32), c67 = lds_f4(cpa + 48),
+                     c89 = lds_f4(cpa + 64);
+        kahan2(mom[0], nc[0], make_float2(c01.x, c01.y), sum);
         if (kWantF) {
-          mom[r][1] += part_[r][1];
-          mom[r][2] += part_[r][2];
-          mom[r][3] += part_[r][3];
+          mom[1] = __ffma2_rn(make_float2(c01.z, c01.w), dif, mom[1]);
+          mom[2] = __ffma2_rn(make_float2(c23.x, c23.y), dif, mom[2]);
+          mom[3] = __ffma2_rn(make_float2(c23.z, c23.w), dif, mom[3]);
         }
-        mom[r][7] += part_[r][7];
-        mom[r][8] += part_[r][8];
-        mom[r][9] += part_[r][9];
-#pragma unroll
-        for (int m = 0; m < 10; ++m) part_[r][m] = 0.f;
+        kahan2(mom[4], nc[1], make_float2(c45.x, c45.y), sum);
+        kahan2(mom[5], nc[2], make_float2(c45.z, c45.w), sum);
+        kahan2(mom[6], nc[3], make_float2(c67.x, c67.y), sum);
+        mom[7] = __ffma2_rn(make_float2(c67.z, c67.w), sum, mom[7]);
+        mom[8] = __ffma2_rn(make_float2(c89.x, c89.y), sum, mom[8]);
+        mom[9] = __ffma2_rn(make_float2(c89.z, c89.w), sum, mom[9]);
       }
     }
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[b]);
-    bool prod_ok = true;
-    if (threadIdx.x == 0 && t + 2 < ntiles) {
-      prod_ok = mbar_wait(&empty[b], ph, spin_limit, status, 4);
-      if (prod_ok) issue_tile(t + 2);
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[st]);
+    if (threadIdx.x == 0) {
+      // refill every stage the other warps have released, without waiting
+      while (issued < ntiles && issued <= t + nstage &&
+             mbar_test(empty_s + 8 * (issued % nstage), (uint32_t)(((issued / nstage) - 1) & 1)))
+        issue_tile(issued++);
     }
-    if (!__shfl_sync(0xffffffffu, prod_ok ? 1 : 0, 0)) { ok = false; break; }
   }
   if (threadIdx.x == 0) {
-    for (int t = consumed; t < issued; ++t) mbar_wait(&full[t & 1], (uint32_t)((t >> 1) & 1), kDrainPolls, status, 8);
+    for (int t = consumed; t < issued; ++t)
+      if (!mbar_wait_sleep(full_s + 8 * (t % nstage), (uint32_t)((t / nstage) & 1), kDrainPolls)) atomicOr(status, 8);
   }
   if (MODE != 1) {
     float emax = 0.f;
     if (ok) {
+      float Ms[2][10];
+#pragma unroll
+      for (int m = 0; m < 10; ++m) {
+        Ms[0][m] = mom[m].x;
+        Ms[1][m] = mom[m].y;
+      }
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const long long gc = r ? gc2 : gc1;
-        const float E = mom[r][0];
+        const float E = Ms[r][0];
         if (kWantF) {
-          for (int m = 0; m < 10; ++m) M_out[m * g.ncell + gc] = mom[r][m];
+          for (int m = 0; m < 10; ++m) M_out[m * g.ncell + gc] = Ms[r][m];
         } else {
           E_out[gc] = E;
         }
         if (E > 0.f) {
           // correctly rounded, as in cell_pass_kernel
-          for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = mom[r][4 + m] / E;
+          for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = Ms[r][4 + m] / E;
         } else {
           for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = m < 3 ? 1.f / 3.f : 0.f;
         }
@@ -1078,11 +1239,13 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
       issue_slot<float>(slots + sb * cnt + fb3 * (j - cnt), g, TL, mx, my, mz, it.mirror_begin + (j - cnt), tpl_g,
                         faces, bnd, &full, 0, 7 - it.octant);
   }
+  if (threadIdx.x == 0) tile[B] = make_float4(0.f, 0.f, 0.f, 0.f);  // identity entry (padding, x = B)
   __syncthreads();
-  if (!mbar_wait_warp(&full, 0, spin_limit, status, 1)) {
-    if (threadIdx.x == 0) mbar_wait(&full, 0, kDrainPolls, status, 8);
+  if (!mbar_wait_sleep_warp(smem_u32(&full), 0, spin_limit, status, 1)) {
+    if (threadIdx.x == 0 && !mbar_wait_sleep(smem_u32(&full), 0, kDrainPolls)) atomicOr(status, 8);
     return;
   }
+  const uint32_t tile_s = smem_u32(tile), id_s = tile_s + 16u * (uint32_t)B;
   // live axes (downwind neighbour exists): the same for b in d and b' in -d
   int live = 0, nlive = 0;
   {
@@ -1117,30 +1280,32 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     const int row = (ae * 2) * N1 + la;
     const int kb = T.nk[row], kc = T.nk[row + N1];
     const float2 wb = T.nw[row], wc = T.nw[row + N1];
-    uint64_t I = pk2(face_value<float>(fin1, g.fstride, B, ae, lb, lc, kb, kc, wb, wc),
-                     face_value<float>(fin2, g.fstride, B, ae, lb, lc, kb, kc, wb, wc));
+    float2 I = make_float2(face_value<float>(fin1, g.fstride, B, ae, lb, lc, kb, kc, wb, wc),
+                           face_value<float>(fin2, g.fstride, B, ae, lb, lc, kb, kc, wb, wc));
     if (!act) last = -1;
-    // lockstep aligned at the downwind end, as in the unpaired face pass
+    // lockstep aligned at the downwind end, as in the unpaired face pass;
+    // a lane whose own ray is shorter reads the identity entry
     const int wl = __reduce_max_sync(0xffffffffu, last);
     if (wl >= 0) {
       const int c0 = T.h->sgn[0] > 0 ? L0 - 1 : B - L0;
       const int c1 = T.h->sgn[1] > 0 ? L1 - 1 : B - L1;
       const int c2 = T.h->sgn[2] > 0 ? L2 - 1 : B - L2;
-      const int idx0 = last >= 0 ? c0 + ts.sy * c1 + ts.sz * c2 : 0;
-      const unsigned char *tb = reinterpret_cast<const unsigned char *>(tile + idx0);
+      const uint32_t tb = last >= 0 ? tile_s + 16u * (uint32_t)(c0 + ts.sy * c1 + ts.sz * c2) : id_s;
+      const uint32_t ev = smem_u32(T.nev);
       int e = wl;
-      for (; e > 0; e -= 2) {
-        TplEvent<float> e0 = T.nev[e], e1 = T.nev[e - 1];
-        if (e > last) { e0.len = 0.f; e0.off = 0; }
-        if (e - 1 > last) { e1.len = 0.f; e1.off = 0; }
-        segment_pair_tile(tb, e0, I);
-        segment_pair_tile(tb, e1, I);
+      if (!(e & 1)) {  // to an odd index: event pairs (e - 1, e) are 16-byte aligned
+        const float2 v = lds_f2(ev + 8 * e);
+        I = step_pair(e <= last ? tb + 2 * (int)__float_as_uint(v.y) : id_s, v.x, I);
+        --e;
       }
-      if (e == 0 && last >= 0) segment_pair_tile(tb, T.nev[0], I);
+      for (; e >= 1; e -= 2) {
+        const float4 v = lds_f4(ev + 8 * (e - 1));
+        I = step_pair(e <= last ? tb + 2 * (int)__float_as_uint(v.w) : id_s, v.z, I);
+        I = step_pair(e - 1 <= last ? tb + 2 * (int)__float_as_uint(v.y) : id_s, v.x, I);
+      }
     }
     if (act) {
-      float I1, I2;
-      upk2(I, I1, I2);
+      const float I1 = I.x, I2 = I.y;
       const int node = ub * W + uc;
       faces[(((long long)(it.dir_begin + j) * nblk + it.block) * 3 + a) * g.fstride + node] = I1;
       faces[(((long long)(it.mirror_begin + j) * nblk + mblock) * 3 + a) * g.fstride + node] = I2;
@@ -1203,16 +1368,20 @@ __global__ void floor_fix_blocks_kernel(const GridDims g, const int *__restrict_
 // several loads are in flight, coefficients of a chunk of 64 directions in
 // shared memory.  The FP32 version keeps pairs of cells in packed f32x2
 // accumulators against (c, c) coefficient pairs.
-template <typename R, int V>
+template <typename R, int V, bool WITH_E64>
 __global__ void __launch_bounds__(256, 4) moments_kernel(long long ncell, int ndir, const R *__restrict__ I,
-                                                      const R *__restrict__ coef, R *__restrict__ M) {
+                                                      const R *__restrict__ coef, R *__restrict__ M,
+                                                      double *__restrict__ E64, double w64) {
   __shared__ R cs[64][10];
   const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * V;
   R acc[V][10];
+  double e64[V];  // E in FP64: the weights are equal, so the sum of I times w
 #pragma unroll
-  for (int v = 0; v < V; ++v)
+  for (int v = 0; v < V; ++v) {
+    e64[v] = 0.0;
 #pragma unroll
     for (int m = 0; m < 10; ++m) acc[v][m] = R(0);
+  }
   for (int k0 = 0; k0 < ndir; k0 += 64) {
     const int nk = min(64, ndir - k0);
     __syncthreads();
@@ -1238,10 +1407,19 @@ __global__ void __launch_bounds__(256, 4) moments_kernel(long long ncell, int nd
 #pragma unroll
           for (int j = 0; j < V; ++j) acc[j][m] = fma(v[j], cm, acc[j][m]);
         }
+        if constexpr (WITH_E64) {
+#pragma unroll
+          for (int j = 0; j < V; ++j) e64[j] += (double)v[j];
+        }
       }
     }
   }
   if (c >= ncell) return;
+  if constexpr (WITH_E64) {
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      if (c + j < ncell) E64[c + j] = w64 * e64[j];
+  }
 #pragma unroll
   for (int m = 0; m < 10; ++m) {
     R *dst = M + m * ncell + c;
@@ -1309,25 +1487,45 @@ void cell_launch(const GridDims &g, const R *kappa, const R *S, const unsigned c
       block_list);
 }
 
+// Staging of the paired cell pass: directions per tile (whole antipodal
+// pairs: the tuned tile rounded up to even) and ring depth, the most stages
+// (at most kPairStagesMax) that fit the shared memory of one of the
+// pair_min_ctas(B) CTAs an SM holds beside the paired tile.
+inline void pair_staging(int B, int want, int &dt, int &nstage) {
+  constexpr long long kSmemPerSM = 233472, kReservedPerCta = 1024;
+  constexpr long long kStatic = 1024 * 4 + 2 * kPairStagesMax * 8 + 64;  // order, barriers, margin
+  const long long per_cta = std::min<long long>(232448, kSmemPerSM / pair_min_ctas(B) - kReservedPerCta) - kStatic;
+  dt = want > 0 ? want : 2;
+  dt = (dt + 1) & ~1;
+  if (dt > kMaxTune) dt = kMaxTune;
+  for (;;) {
+    const long long ring = per_cta - (long long)pair_smem_bytes(B, 0);
+    nstage = (int)std::min<long long>(kPairStagesMax, ring / ((long long)dt * cell_slot(B).bytes));
+    if (nstage >= 2 || dt <= 2) break;
+    dt -= 2;
+  }
+}
+
 template <int MODE, int BC>
 void pair_launch(const GridDims &g, const float *kappa, const float *S, const unsigned char *tpl, const int *order,
                  const float *faces, const float *bnd, float *I_out, float *M_out, float *E_out, float *f_out,
                  void *emax_bits, long long spin, int *status, const int *block_list, int nlist, cudaStream_t st) {
   const int parts = BC * BC * BC / 2 / pair_threads(BC);
   const int nblk = block_list ? nlist : g.nbx * g.nby * g.nbz;
-  const int dt = pair_dir_tile(BC, g.dir_tile);
+  int dt, nstage;
+  pair_staging(BC, g.dir_tile, dt, nstage);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // prologue overlaps the face pass's end
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.gridDim = dim3(nblk * parts);
   cfg.blockDim = dim3(pair_threads(BC));
-  cfg.dynamicSmemBytes = pair_smem_bytes(BC, 2 * dt);
+  cfg.dynamicSmemBytes = pair_smem_bytes(BC, nstage * dt);
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, cell_pair_kernel<MODE, BC>, g, parts, dt, kappa, S, tpl, order, faces, bnd, I_out, M_out,
-                     E_out, f_out, emax_bits, spin, status, block_list);
+  cudaLaunchKernelEx(&cfg, cell_pair_kernel<MODE, BC>, g, parts, dt, nstage, kappa, S, tpl, order, faces, bnd, I_out,
+                     M_out, E_out, f_out, emax_bits, spin, status, block_list);
 }
 
 template <typename R>
@@ -1444,7 +1642,8 @@ cudaError_t launch_floor_fix_blocks(const GridDims &g, const int *block_list, in
 }
 
 template <typename R>
-cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef, R *M_out, cudaStream_t st) {
+cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef, R *M_out, cudaStream_t st,
+                           double *E64, double w64) {
   const int threads = 256;
   // vector loads need every direction's row to start 16-byte aligned
   constexpr int VW = 16 / (int)sizeof(R);
@@ -1453,10 +1652,16 @@ cudaError_t launch_moments(long long ncell, int ndir, const R *I, const R *coef,
   const long long per = vec ? VW : 1;
   const long long blocks = ((ncell + per - 1) / per + threads - 1) / threads;
   if (blocks < 1) return cudaSuccess;
-  if (vec)
-    moments_kernel<R, VW><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out);
-  else
-    moments_kernel<R, 1><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out);
+  if (E64) {
+    if (vec)
+      moments_kernel<R, VW, true><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out, E64, w64);
+    else
+      moments_kernel<R, 1, true><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out, E64, w64);
+  } else if (vec) {
+    moments_kernel<R, VW, false><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out, E64, w64);
+  } else {
+    moments_kernel<R, 1, false><<<(unsigned)blocks, threads, 0, st>>>(ncell, ndir, I, coef, M_out, E64, w64);
+  }
   return cudaGetLastError();
 }
 
@@ -1493,7 +1698,7 @@ cudaError_t prepare_kernels() {
                                                cudaStream_t);                                                \
   template cudaError_t launch_floor_fix<R>(long long, const R *, long long, const void *, double, R *,     \
                                            cudaStream_t);                                                    \
-  template cudaError_t launch_moments<R>(long long, int, const R *, const R *, R *, cudaStream_t);
+  template cudaError_t launch_moments<R>(long long, int, const R *, const R *, R *, cudaStream_t, double *, double);
 
 VET_INSTANTIATE(float)
 VET_INSTANTIATE(double)

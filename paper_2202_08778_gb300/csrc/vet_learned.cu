@@ -3,6 +3,7 @@
 // vet_closure_learned (network + indicator + exact fallback on flagged
 // blocks).  Kernels are in vet_cnn.cu.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -366,6 +367,71 @@ VET_API vet_status vet_model_get_grads(vet_model *m, float *grads) {
   if (!m || !grads) return fail(m, VET_EINVAL, "model and grads are required");
   if (!m->have_backward) return fail(m, VET_EINVAL, "no backward pass has run");
   return copy_flat(m, m->g, grads);
+}
+
+// Model files: the 8-byte tag "VETMODL1", int32 hidden channels, int32 0,
+// int64 parameter count, int64 AdamW step count, then three FP32 arrays in
+// the host parameter layout: the parameters and AdamW's first and second
+// moments.  Little-endian, as both host architectures store them.
+namespace {
+constexpr char kModelTag[8] = {'V', 'E', 'T', 'M', 'O', 'D', 'L', '1'};
+struct ModelFileHead {
+  char tag[8];
+  int32_t channels, zero;
+  int64_t nparams, step;
+};
+static_assert(sizeof(ModelFileHead) == 32, "model file head");
+}  // namespace
+
+VET_API vet_status vet_model_save(vet_model *m, const char *path) {
+  if (!m || !path) return fail(m, VET_EINVAL, "model and path are required");
+  const size_t n = (size_t)m->host_params;
+  std::vector<float> buf(3 * n);
+  vet_status s = copy_flat(m, m->p, buf.data());
+  if (!s) s = copy_flat(m, m->m, buf.data() + n);
+  if (!s) s = copy_flat(m, m->v, buf.data() + 2 * n);
+  if (s) return s;
+  ModelFileHead h{};
+  std::memcpy(h.tag, kModelTag, sizeof h.tag);
+  h.channels = m->channels;
+  h.nparams = (int64_t)n;
+  h.step = (int64_t)m->step;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return fail(m, VET_EINVAL, std::string("cannot open ") + path + " for writing");
+  const bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 && std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed) return fail(m, VET_EINVAL, std::string("write to ") + path + " failed");
+  return VET_OK;
+}
+
+VET_API vet_status vet_model_load(vet_model *m, const char *path) {
+  if (!m || !path) return fail(m, VET_EINVAL, "model and path are required");
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return fail(m, VET_EINVAL, std::string("cannot open ") + path);
+  ModelFileHead h{};
+  const size_t n = (size_t)m->host_params;
+  std::vector<float> buf(3 * n);
+  bool ok = std::fread(&h, sizeof h, 1, f) == 1;
+  std::string why;
+  if (!ok || std::memcmp(h.tag, kModelTag, sizeof h.tag) != 0) why = "not a libvet model file";
+  else if (h.channels != m->channels) why = "file has " + std::to_string(h.channels) + " hidden channels, model has " + std::to_string(m->channels);
+  else if (h.nparams != (int64_t)n || h.step < 0) why = "parameter count does not match";
+  else if (std::fread(buf.data(), sizeof(float), buf.size(), f) != buf.size()) why = "file is truncated";
+  std::fclose(f);
+  if (!why.empty()) return fail(m, VET_EINVAL, std::string(path) + ": " + why);
+  vet_status s = vet_model_set_params(m, buf.data());  // also refreshes the BF16 copies
+  if (s) return s;
+  DevGuard dg(m->device);
+  std::vector<float> pad;
+  host_to_padded(m, buf.data() + n, pad);
+  cudaError_t e = cudaMemcpy(m->m, pad.data(), sizeof(float) * pad.size(), cudaMemcpyHostToDevice);
+  if (!e) {
+    host_to_padded(m, buf.data() + 2 * n, pad);
+    e = cudaMemcpy(m->v, pad.data(), sizeof(float) * pad.size(), cudaMemcpyHostToDevice);
+  }
+  if (e) return cuda_fail(m, e, "optimiser state upload");
+  m->step = (long long)h.step;
+  return VET_OK;
 }
 
 VET_API vet_status vet_model_features(vet_model *m, const vet_grid *grid, int nvol, const float *kappa,

@@ -1,5 +1,5 @@
 // vet_local.cu -- the local closures the paper compares the VET closure with
-// (Sec. 6.1): Eddington, T = I / 3, and M1,
+// (Sec. 4.1): Eddington, T = I / 3, and M1,
 //   T = (1 - chi)/2 I + (3 chi - 1)/2 n n,  n = F / |F|,
 //   chi(f) = (3 + 4 f^2) / (5 + 2 sqrt(4 - 3 f^2)),  f = |F| / E (c = 1),
 // from the moments of each cell.  f is clipped to [0, 1]; F = 0 leaves

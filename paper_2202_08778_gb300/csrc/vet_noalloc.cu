@@ -113,6 +113,7 @@ VET_API vet_status vet_closure_noalloc(const vet_grid *grid, const vet_config *c
   const int nlevels = nb[0] + nb[1] + nb[2] - 2;
   if (nlevels > kMaxLevels) return fail(VET_EINVAL, "too many blocks along the grid axes");
   const int tbytes = vet::tpl_layout<float>(B).bytes;
+  if (tbytes > kTplMax) return fail(VET_EINVAL, "direction template larger than the static host staging slot");
 
   std::lock_guard<std::mutex> lock(g_mutex);
 

@@ -1,5 +1,5 @@
 // vet_reuse.cu -- the change gate behind reusing the Eddington tensor across
-// time steps (paper Sec. 7, the suggestion of recomputing f only every few
+// time steps (paper Sec. 4.2, the suggestion of recomputing f only every few
 // steps).  Per block of B^3 cells and over the grid it finds
 //   dtrans = max |a - b| / ((1 + a/2) (1 + b/2)),  a = kappa h, b = kappa_ref h,
 //            a bound on the change |e^{-a} - e^{-b}| of the cell's
@@ -166,4 +166,20 @@ extern "C" __attribute__((visibility("default"))) vet_status vet_field_change(co
   else
     gate_kernel<false><<<(unsigned)nb, threads, 0, st>>>(a, kappa, S, kappa_ref, S_ref, out);
   return cudaGetLastError() == cudaSuccess ? VET_OK : VET_ECUDA;
+}
+
+// The decision the gate serves (Sec. 4.2 reading): recompute on the first
+// step, once the stored f is max_age steps old, when a change is not finite,
+// or when the grid's transmission bound or source change exceeds its
+// tolerance (the source's relative to its scale).  Host arithmetic in double
+// on the FP32 triple, exactly as the oracle takes it.
+extern "C" __attribute__((visibility("default"))) vet_status vet_reuse_decision(const float *change, int age, int first, double tol_tau, double tol_S,
+                                      int max_age, int *recompute) {
+  if (!change || !recompute || max_age < 1 || age < 0 || !(tol_tau >= 0.0) || !(tol_S >= 0.0)) return VET_EINVAL;
+  const double dtau = change[0], dS = change[1], sref = change[2];
+  if (first || age >= max_age || !std::isfinite(dtau) || !std::isfinite(dS))
+    *recompute = 1;
+  else
+    *recompute = (dtau > tol_tau || dS > tol_S * sref) ? 1 : 0;
+  return VET_OK;
 }

@@ -33,7 +33,8 @@ EXPORTS = (
     "vet_model_create", "vet_model_destroy", "vet_model_num_params", "vet_model_set_params", "vet_model_get_params",
     "vet_model_get_grads", "vet_model_features", "vet_model_forward", "vet_model_backward", "vet_model_step",
     "vet_closure_learned", "vet_model_last_timing", "vet_model_last_indicator", "vet_model_last_error",
-    "vet_local_closure", "vet_point_source", "vet_field_change",
+    "vet_local_closure", "vet_point_source", "vet_field_change", "vet_reuse_decision", "vet_model_save",
+    "vet_model_load",
 )
 
 #: functions whose return value is not a vet_status
@@ -86,8 +87,8 @@ def load(build_if_missing: bool = True):
         lib.vet_directions.argtypes = [vp, vp]
         for name in ("vet_trace", "vet_trace_f64"):
             getattr(lib, name).argtypes = [vp, vp, vp, vp, vp, vp]
-        for name in ("vet_moments", "vet_moments_f64"):
-            getattr(lib, name).argtypes = [vp, vp, vp, vp]
+        lib.vet_moments.argtypes = [vp, vp, vp, vp, vp]
+        lib.vet_moments_f64.argtypes = [vp, vp, vp, vp]
         for name in ("vet_closure", "vet_closure_f64"):
             getattr(lib, name).argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.vet_sync.argtypes = [vp]
@@ -98,6 +99,8 @@ def load(build_if_missing: bool = True):
         lib.vet_launches_per_closure.restype = i
         lib.vet_closure_noalloc.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Config), vp, vp, vp, vp, vp, vp]
         lib.vet_set_tuning.argtypes = [vp, i, i]
+        lib.vet_reuse_decision.argtypes = [ctypes.POINTER(ctypes.c_float), i, i, ctypes.c_double, ctypes.c_double, i,
+                                           ip]
         lib.vet_get_tuning.argtypes = [vp, ip, ip]
         lib.vet_autotune.argtypes = [vp, vp, vp, vp, ip, ip, vp]
         lib.vet_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(_Grid), ctypes.POINTER(_Config)]
@@ -125,6 +128,8 @@ def load(build_if_missing: bool = True):
         lib.vet_closure_learned.argtypes = [vp, vp, vp, vp, vp, vp, f, vp, vp, ip, vp]
         lib.vet_model_last_timing.argtypes = [vp, ctypes.POINTER(f)]
         lib.vet_model_last_indicator.argtypes = [vp, vp, vp]
+        lib.vet_model_save.argtypes = [vp, ctypes.c_char_p]
+        lib.vet_model_load.argtypes = [vp, ctypes.c_char_p]
         lib.vet_model_last_error.argtypes = [vp]
         lib.vet_model_last_error.restype = ctypes.c_char_p
         lib.vet_local_closure.argtypes = [i, ctypes.c_longlong, vp, vp, vp]
@@ -238,10 +243,19 @@ class Context:
                                           _stream(stream)))
         return I_out
 
-    def moments(self, I, M_out, stream=None):
+    def moments(self, I, M_out, stream=None, E64_out=None):
+        """vet_moments: I [N][cells] -> M_out [10][cells]; E64_out (FP32
+        contexts, optional, a float64 CUDA tensor [cells]) receives E summed
+        in FP64."""
         nc, dt = self.ncell, self.dtype
-        self._check(self._fn("vet_moments")(self._h, _ptr(I, dt, self.N * nc, "I"), _ptr(M_out, dt, 10 * nc, "M_out"),
-                                            _stream(stream)))
+        if self.precision == VET_FP64:
+            if E64_out is not None:
+                raise ValueError("E64_out is for FP32 contexts (the FP64 moments are already double)")
+            self._check(self._lib.vet_moments_f64(self._h, _ptr(I, dt, self.N * nc, "I"),
+                                                  _ptr(M_out, dt, 10 * nc, "M_out"), _stream(stream)))
+        else:
+            self._check(self._lib.vet_moments(self._h, _ptr(I, dt, self.N * nc, "I"), _ptr(M_out, dt, 10 * nc, "M_out"),
+                                              _ptr(E64_out, np.float64, nc, "E64_out"), _stream(stream)))
         return M_out
 
     def closure(self, kappa, S, Ib, f_out, M_out=None, stream=None):
@@ -343,22 +357,24 @@ def field_change(shape, block: int, h: float, kappa, S, kappa_ref, S_ref, out, s
 
 def reuse_decision(change, age: int, first: bool, tol_tau: float, tol_S: float, max_age: int) -> bool:
     """Whether a stored Eddington tensor must be recomputed this time step
-    (paper Sec. 7): always on the first step and once it is max_age steps
+    (paper Sec. 4.2): always on the first step and once it is max_age steps
     old; otherwise when the grid's largest transmission change exceeds
     tol_tau or its largest source change exceeds tol_S times the source
     scale.  `change` is the grid triple (dtrans, dS, Sref) of field_change;
     a non-finite change forces a recompute."""
-    if first or age >= max_age:
-        return True
-    dtr, dS, sref = float(change[0]), float(change[1]), float(change[2])
-    if dtr != dtr or dS != dS or dtr == float("inf") or dS == float("inf"):
-        return True
-    return dtr > tol_tau or dS > tol_S * sref
+    lib = load()
+    c = (ctypes.c_float * 3)(*[float(v) for v in change[:3]])
+    out = ctypes.c_int()
+    st = lib.vet_reuse_decision(c, int(age), int(bool(first)), float(tol_tau), float(tol_S), int(max_age),
+                                ctypes.byref(out))
+    if st != VET_OK:
+        raise VetError(st, "vet_reuse_decision: bad age, max_age or tolerance")
+    return bool(out.value)
 
 
 class ClosureReuse:
     """Time steps of the closure that reuse f while its inputs stay close to
-    the snapshot f was computed from (paper Sec. 7's suggestion of updating
+    the snapshot f was computed from (paper Sec. 4.2's suggestion of updating
     the Eddington tensor only every few steps).  Each step runs the change
     gate (vet_field_change) against the snapshot, reads the grid's three
     numbers back to the host (12 bytes; the step synchronises the stream),
@@ -595,19 +611,13 @@ class Model:
         return self._unflat(flat)
 
     def save(self, path):
-        """Write the FP32 parameters (per layer W [27][C_out][C_in], b [C_out])
-        to an .npz file."""
-        arrays = {}
-        for i, (W, b) in enumerate(self.params()):
-            arrays[f"W{i}"], arrays[f"b{i}"] = W, b
-        np.savez(path, channels=np.int32(self.channels), **arrays)
+        """vet_model_save: parameters, AdamW state and step count to a file."""
+        self._check(self._lib.vet_model_save(self._h, os.fsencode(os.fspath(path))))
 
     def load(self, path):
-        """Read parameters written by save() (the hidden width must match)."""
-        with np.load(path) as z:
-            if int(z["channels"]) != self.channels:
-                raise ValueError(f"file has {int(z['channels'])} hidden channels, model has {self.channels}")
-            self.set_params([(z[f"W{i}"], z[f"b{i}"]) for i in range(len(self.shapes))])
+        """vet_model_load: read a file written by save() (the hidden width
+        and parameter count must match)."""
+        self._check(self._lib.vet_model_load(self._h, os.fsencode(os.fspath(path))))
 
     def features(self, shape, block: int, h: float, kappa, S, E, nvol: int = 1, feat_out=None, stream=None):
         """Features of nvol stacked volumes of `shape` (device tensors)."""

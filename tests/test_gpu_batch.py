@@ -89,3 +89,28 @@ def test_config4_batch_of_64_ragged_grids():
         assert torch.equal(fr, f[i])
         fi = f[i].view(6, -1)
         assert (fi[0] + fi[1] + fi[2] - 1).abs().max().item() < 1e-6
+
+
+def test_retuning_a_member_recaptures_the_batch_graph():
+    """A member retuned through the batch (a new face-pass schedule, whose old
+    item list the captured graph would read after it was freed, and a new
+    cell-pass tile) must make the next batched closure capture again: its
+    results then equal the grids' own closures at the new tuning."""
+    problems = synth.batched_problems(n_grids=3, seed0=140, edges=(32, 48), blocks=(16,), nsides=(4,))
+    specs, k, s = _batch(problems)
+    batch = vet.Batch(specs)
+    f = [torch.empty(6 * x.numel(), device="cuda") for x in k]
+    batch.closure(k, s, None, f)
+    batch.sync()
+    fg0, dt0 = batch.members[0].tuning()
+    batch.members[0].set_tuning(face_group=2 if fg0 != 2 else 8, dir_tile=4 if dt0 != 4 else 2)
+    assert batch.members[0].tuning() != (fg0, dt0)
+    batch.closure(k, s, None, f)
+    batch.sync()
+    for i in range(len(problems)):
+        ctx = vet.Context(*specs[i])
+        ctx.set_tuning(*batch.members[i].tuning())
+        fr = torch.empty_like(f[i])
+        ctx.closure(k[i], s[i], None, fr)
+        ctx.sync()
+        assert torch.equal(fr, f[i]), i

@@ -180,8 +180,8 @@ def test_save_and_load_round_trip(tmp_path):
     kappa, S, E = _fields(rng, 1, (8, 8, 8))
     a, b = vet.Model(), vet.Model()
     a.set_params(_params(15))
-    a.save(tmp_path / "net.npz")
-    b.load(tmp_path / "net.npz")
+    a.save(tmp_path / "net.vetm")
+    b.load(tmp_path / "net.vetm")
     for (Wa, ba), (Wb, bb) in zip(a.params(), b.params()):
         np.testing.assert_array_equal(Wa, Wb)
         np.testing.assert_array_equal(ba, bb)
@@ -193,9 +193,50 @@ def test_save_and_load_round_trip(tmp_path):
         torch.cuda.synchronize()
         outs.append(o.cpu().numpy())
     np.testing.assert_array_equal(outs[0], outs[1])
-    np.savez(tmp_path / "other.npz", channels=np.int32(16))
-    with pytest.raises(ValueError):
-        b.load(tmp_path / "other.npz")
+    # a file of another hidden width, a truncated file and a foreign file are
+    # refused, and the model keeps its parameters
+    raw = (tmp_path / "net.vetm").read_bytes()
+    assert raw[:8] == b"VETMODL1" and int.from_bytes(raw[8:12], "little") == 32
+    (tmp_path / "other.vetm").write_bytes(raw[:8] + (16).to_bytes(4, "little") + raw[12:])
+    (tmp_path / "short.vetm").write_bytes(raw[: len(raw) // 2])
+    (tmp_path / "foreign.vetm").write_bytes(b"NOTAMODEL" + raw[9:])
+    for name in ("other.vetm", "short.vetm", "foreign.vetm"):
+        with pytest.raises(vet.VetError):
+            b.load(tmp_path / name)
+    for (Wa, ba), (Wb, bb) in zip(a.params(), b.params()):
+        np.testing.assert_array_equal(Wa, Wb)
+
+
+def test_checkpoint_resumes_training(tmp_path):
+    """Saving after some AdamW steps and loading into a fresh model carries
+    the optimiser state and step count: the next step gives the same
+    parameters in both models (to the rounding of the weight gradient's
+    atomic sums), unlike a model given the parameters alone, whose AdamW
+    restarts from zero moments."""
+    rng = np.random.default_rng(16)
+    kappa, S, E = _fields(rng, 1, (8, 8, 8))
+    f_ref = _dev(rng.uniform(-0.1, 0.4, (6, 512)).astype(np.float32))
+    a = vet.Model()
+    a.set_params(_params(16))
+
+    def train_step(m):
+        m.features((8, 8, 8), 4, 0.125, _dev(kappa), _dev(S), _dev(E))
+        m.forward()
+        m.backward(f_ref, lam=0.01)
+        m.step(lr=1e-3)
+
+    for _ in range(3):
+        train_step(a)
+    a.save(tmp_path / "ckpt.vetm")
+    b, c = vet.Model(), vet.Model()
+    b.load(tmp_path / "ckpt.vetm")
+    c.set_params(a.params())
+    for m in (a, b, c):
+        train_step(m)
+    flat = lambda m: np.concatenate([np.concatenate([W.ravel(), bb.ravel()]) for W, bb in m.params()])
+    pa, pb, pc = flat(a), flat(b), flat(c)
+    assert np.abs(pa - pb).max() < 1e-6
+    assert np.abs(pa - pc).max() > 1e-5
 
 
 def test_indicator_closed_form_with_bias_only_network():
@@ -315,6 +356,7 @@ def test_learned_closure_with_fallback(trained):
     f = torch.empty(6 * n, device="cuda")
     flags = torch.zeros(nblk, dtype=torch.int32, device="cuda")
     f_plain = torch.empty(6 * n, device="cuda")
+    kept = 0
     for v in range(held[0].shape[0]):
         k, S, E, f_tr = held[0][v], held[1][v], held[2][v], held[3][v]
         nfb = m.closure(ctx, k, S, E, f, threshold=1e-2, block_flags=flags)
@@ -332,8 +374,15 @@ def test_learned_closure_with_fallback(trained):
         assert np.array_equal(got[:, cell_flag], ref[:, cell_flag])
         err = np.abs(got - ref).max()
         print(f"held-out {v}: {nfb}/{nblk} blocks recomputed, max |f - f_traced| = {err:.3e}")
+        # the accuracy contract: every block the network keeps is within 1e-2
+        # of the traced tensor in every component
+        assert err <= 1e-2, err
+        kept += nblk - nfb
     # without fallback the result is the network's tensor everywhere
     nfb = m.closure(ctx, held[0][0], held[1][0], held[2][0], f, threshold=float("inf"), block_flags=flags)
     assert nfb == 0 and int(flags.sum()) == 0
     f_net = _net_f(m, held[0][0], held[1][0], held[2][0])
     assert np.abs(f.cpu().numpy().reshape(6, -1) - f_net).max() < 1e-6
+    if kept == 0:
+        pytest.xfail("the network kept no block at 1e-2 on the held-out fields: every block fell back to the "
+                     "exact closure (the contract held trivially)")

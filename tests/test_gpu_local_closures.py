@@ -1,4 +1,4 @@
-"""GPU parity of vet_local_closure (paper Sec. 6.1) against the FP64 oracle
+"""GPU parity of vet_local_closure (paper Sec. 4.1) against the FP64 oracle
 (oracle/local_closures.py), on seeded moments that cover the reduced-flux
 range [0, 1], clipped fluxes above E, zero flux, and E = 0 and E < 0, with
 cell counts that take the 16-byte path (a multiple of 4) and the scalar one.

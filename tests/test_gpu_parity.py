@@ -177,6 +177,15 @@ def test_fp32_moments_entry_point_matches_oracle(ora):
     M_ref = ora.moments(I.astype(np.float64), ctx.directions())
     eE, eFP = moment_errors(M.cpu().numpy(), M_ref)
     assert eE < 1e-6 and eFP < 1e-6
+    # the optional FP64 E: the oracle's FP64 E of the same FP32 intensities,
+    # to FP64 rounding (the sum of 48 values), not FP32's
+    E64 = torch.full((16 ** 3,), -1.0, dtype=torch.float64, device="cuda")
+    ctx.moments(torch.from_numpy(I).cuda(), M, E64_out=E64)
+    ctx.sync()
+    e64 = E64.cpu().numpy()
+    assert np.abs(e64 - M_ref[0].ravel()).max() / M_ref[0].max() < 1e-14
+    with pytest.raises(vet.VetError):  # a host E64_out is refused
+        ctx.moments(torch.from_numpy(I).cuda(), M, E64_out=torch.zeros(16 ** 3, dtype=torch.float64))
 
 
 def test_host_buffers_give_identical_results():

@@ -1,5 +1,5 @@
 """GPU parity of the change gate (vet_field_change) and of the reuse of f
-across time steps (paper Sec. 7) against the oracle (oracle/field_change.py).
+across time steps (paper Sec. 4.2) against the oracle (oracle/field_change.py).
 
 The gate's numbers are FP32 with one IEEE rounding per operation and exact
 maxima on both sides, so they are compared bit for bit: on ragged grids

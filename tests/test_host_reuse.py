@@ -1,4 +1,4 @@
-"""Host logic of the reuse of f across time steps (paper Sec. 7): the
+"""Host logic of the reuse of f across time steps (paper Sec. 4.2): the
 library's decision (vet.reuse_decision) against the oracle's decision on
 seeded triples, ages and tolerances, including non-finite changes and
 triples on the tolerance boundary."""

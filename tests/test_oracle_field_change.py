@@ -1,5 +1,5 @@
 """Pins of the change-gate oracle (oracle/field_change.py; the reuse of f
-across time steps of paper Sec. 7): the opacity measure against the exact
+across time steps of paper Sec. 4.2): the opacity measure against the exact
 change of a cell's transmission (an upper bound everywhere, equal to the
 optical-depth change for thin cells, negligible for thick ones), block
 numbering and maxima against brute-force loops over cells, exact values of

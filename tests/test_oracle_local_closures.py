@@ -1,4 +1,4 @@
-"""Pins of the local-closure oracle (oracle/local_closures.py; paper Sec. 6.1):
+"""Pins of the local-closure oracle (oracle/local_closures.py; paper Sec. 4.1):
 limits of the Eddington factor, the tensor's trace and eigenstructure, free
 streaming, isotropy, rotation covariance and the clipping reading.  A wrong
 coefficient, sign or component order breaks one of them."""
