@@ -161,7 +161,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(p, dirs, ndir_sample: int):
+def oracle_sample(p, dirs, ndir_sample: int, Ib=None, grid_text: str = "128^3"):
     """Time the FP64 oracle (trace -> moments -> closure) on the workload's
     grid restricted to an evenly spaced subset of directions.  Returns
     (cell-angle updates per second, seconds, threads used, sample text)."""
@@ -175,15 +175,95 @@ def oracle_sample(p, dirs, ndir_sample: int):
     cores = len(os.sched_getaffinity(0))
     k = p["kappa"].astype(np.float32).astype(np.float64)
     s = p["S"].astype(np.float32).astype(np.float64)
+    ib = None if Ib is None else np.ascontiguousarray(Ib[:, idx], dtype=np.float64)
     t0 = time.perf_counter()
-    I = oracle.trace(k, s, sub, p["B"], p["h"], None, nthreads=cores)
+    I = oracle.trace(k, s, sub, p["B"], p["h"], ib, nthreads=cores)
     M = oracle.moments(I, sub)
     oracle.closure(M)
     dt = time.perf_counter() - t0
     upd = k.size * ndir_sample
     return upd / dt, dt, min(cores, ndir_sample), (
-        f"{ndir_sample} of {dirs.shape[0]} directions (evenly spaced) over the full 128^3 grid, "
+        f"{ndir_sample} of {dirs.shape[0]} directions (evenly spaced) over the full {grid_text} grid, "
         f"trace+moments+closure in FP64")
+
+
+def workload_measurement(local_rank, kind: str, steps: int = 10, cpu: bool = True):
+    """One of the two largest single-GPU workloads, timed like the headline
+    (autotuned tiles, L2 flushed between steps, inputs in HBM): "shadow" is
+    the 256x128x128 cloud in 16^3 blocks with 768 directions and the beam
+    through x = 0; "lognormal256" the learned closure's 256^3 lognormal grid
+    (16^3 blocks, 192 directions, seed 3) closed by the plain tracer.  With
+    the cell-pass roofline, the closure through pinned host buffers and the
+    FP64 oracle on a sample of directions over the full grid."""
+    import numpy as np
+    import torch
+
+    from paper_2202_08778_gb300 import synth, vet
+
+    dev = torch.device("cuda", local_rank)
+    if kind == "shadow":
+        p = synth.cloud_problem(nx=256, ny=128, nz=128, B=16, nside=8, seed=3)
+        name, grid_text = "shadow256x128x128_B16_nside8 (beam within 10 deg of +x on x = 0)", "256x128x128"
+    else:
+        p = synth.lognormal_problem(n=256, B=16, nside=4, seed=3)
+        name, grid_text = "lognormal256_B16_nside4 (seed 3)", "256^3"
+    ctx = vet.Context(p["kappa"].shape, p["B"], p["h"], p["nside"], p["q"], device=local_rank)
+    dirs = ctx.directions()
+    Ib = synth.beam_ib(dirs, p["beam_half_angle_deg"]).astype(np.float32) if kind == "shadow" else None
+    n, N = p["kappa"].size, ctx.N
+    k_h = np.ascontiguousarray(p["kappa"].astype(np.float32))
+    s_h = np.ascontiguousarray(p["S"].astype(np.float32))
+    kappa, S = torch.from_numpy(k_h).to(dev), torch.from_numpy(s_h).to(dev)
+    ib = None if Ib is None else torch.from_numpy(Ib).to(dev)
+    f = torch.empty(6 * n, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    tuning = ctx.autotune(kappa, S, ib)
+    for _ in range(3):
+        ctx.closure(kappa, S, ib, f)
+    ctx.set_timing(True)
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    phase = []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        ctx.closure(kappa, S, ib, f)
+        ev[i][1].record(stream)
+        phase.append(ctx.last_timing())
+    torch.cuda.synchronize(dev)
+    ctx.set_timing(False)
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    cell_segs, face_segs = ctx.work_counts()
+    cell_ms = statistics.median(ph[1] for ph in phase)
+    peak = MUFU_PER_CLK_PER_SM * N_SM * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
+    achieved = cell_segs / (cell_ms * 1e-3) / 1e9
+    kp, sp = torch.from_numpy(k_h).pin_memory(), torch.from_numpy(s_h).pin_memory()
+    ibp = None if Ib is None else torch.from_numpy(Ib).pin_memory()
+    fp = torch.empty(6 * n, dtype=torch.float32).pin_memory()
+    ctx.closure(kp, sp, ibp, fp)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        ctx.closure(kp, sp, ibp, fp)
+    e2e_s = (time.perf_counter() - t0) / 3
+    out = {"workload": name, "value": float(n) * N / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+           "steps": steps, "closures_per_s": 1e3 / ms,
+           "tuning": {"face_group": tuning[0], "dir_tile": tuning[1]},
+           "phases_ms": {"face_pass": statistics.median(ph[0] for ph in phase), "cell_pass": cell_ms},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G exp/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "cell_pair_kernel<2,16> (FP32 cell pass on mirrored ray pairs)",
+                        "algorithmic": f"{cell_segs} cell-ray segments (one exp each) per launch"},
+           "e2e": {"value": float(n) * N / e2e_s / 1e9, "unit": UNIT, "ms_per_step": 1e3 * e2e_s,
+                   "h2d_bytes_per_step": 2 * n * 4 + (0 if Ib is None else Ib.nbytes),
+                   "d2h_bytes_per_step": 6 * n * 4}}
+    del ctx, f, flush
+    torch.cuda.empty_cache()
+    if cpu:
+        cores = len(os.sched_getaffinity(0))
+        v, dt, used, sample = oracle_sample(p, dirs, min(N, 2 * cores), Ib, grid_text)
+        out["cpu_baseline"] = {"value": v / 1e9, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                               "seconds": dt}
+    return out
 
 
 def conv_flops_per_cell():
@@ -623,6 +703,10 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_reuse:
         line["reuse"] = reuse_measurement(ctx, flush)
 
+    if rank == 0 and world == 1 and not args.no_large:
+        line["workloads"] = {kind: workload_measurement(local_rank, kind, cpu=not args.no_cpu_baseline)
+                             for kind in ("shadow", "lognormal256")}
+
     if rank == 0 and world == 1 and not args.no_batch:
         line["batch"] = batch_measurement(local_rank)
 
@@ -649,6 +733,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-grid batched-closure measurement")
     ap.add_argument("--no-reuse", action="store_true", help="skip the measurement of reusing f across time steps")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 256x128x128 shadow and 256^3 lognormal workloads")
     ap.add_argument("--tuning", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
                     metavar="FG,DT", help="fixed face-pass direction group and cell-pass direction tile "
                     "instead of autotuning")
