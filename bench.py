@@ -315,6 +315,47 @@ def batch_measurement(local_rank, reps: int = 20):
             "speedup_vs_sequential": t_seq / t_batch}
 
 
+def hlle_measurement(ctx, kappa, S, flush, reps: int = 20):
+    """The HLLE face wavespeed with the optical-depth correction (paper Sec.
+    2.2.3; vet_hlle_wavespeed) from this workload's f and kappa (as rho
+    kappa_R), repeated 8 times along z (16.8M cells), x-normal faces; against
+    the HBM copy bandwidth: per face f_aa and kappa read (4 + 4 bytes, each
+    cell once from DRAM) and the speed written (4 bytes), L2 flushed before
+    every timed launch."""
+    import torch
+
+    from paper_2202_08778_gb300 import vet
+
+    n0 = kappa.numel()
+    nz, ny, nx = 128, 128, 128
+    f0 = torch.empty(6 * n0, dtype=torch.float32, device=kappa.device)
+    ctx.closure(kappa, S, None, f0)
+    f = f0.view(6, n0).repeat(1, 8).reshape(-1)
+    k = kappa.reshape(-1).repeat(8)
+    shape = (8 * nz, ny, nx)
+    nface = 8 * nz * ny * (nx + 1)
+    C = torch.empty(nface, dtype=torch.float32, device=kappa.device)
+    ms = []
+    for i in range(reps + 3):
+        flush.fill_(i & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        vet.hlle_wavespeed(shape, 1.0 / 128, f, k, C, 0)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    nbytes = 8.0 * (8 * n0) + 4.0 * nface
+    gbs = nbytes / (t * 1e-3) / 1e9
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    return {"kernel": "hlle_kernel (vet_hlle_wavespeed, x-normal faces)", "faces": nface,
+            "input": "the workload's f and kappa (as rho kappa_R) repeated 8 times along z", "ms": t,
+            "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "algorithmic": "8 bytes per cell read (f_xx, kappa), 4 bytes per face written",
+            "G_faces_per_s": nface / (t * 1e-3) / 1e9}
+
+
 def local_closure_measurement(ctx, kappa, S, flush, reps: int = 20):
     """The M1 local closure (paper Sec. 4.1; vet_local_closure) on the
     moments of this workload, against the HBM copy bandwidth: 16 bytes read
@@ -660,6 +701,7 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": 6 * n * 4, "ms_per_step": 1e3 * e2e_s}
 
     local = local_closure_measurement(ctx, kappa, S, flush) if rank == 0 and world == 1 else None
+    hlle = hlle_measurement(ctx, kappa, S, flush) if rank == 0 and world == 1 else None
     point = (point_source_measurement(kappa, p["kappa"].shape, p["h"], flush)
              if rank == 0 and world == 1 else None)
 
@@ -694,6 +736,8 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps}
     if local is not None:
         line["local_closure_m1"] = local
+    if hlle is not None:
+        line["hlle_wavespeed"] = hlle
     if point is not None:
         line["point_source"] = point
     clocks = clk.summary()

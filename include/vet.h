@@ -407,6 +407,34 @@ vet_status vet_reuse_decision(const float *change, int age, int first, double to
                               int *recompute);
 
 /* ------------------------------------------------------------------------
+ * HLLE face wavespeed with the optical-depth correction (paper Sec. 2.2.3,
+ * "Implicit Hyperbolic Transport of Radiation", and App. A): the first
+ * consumer of the Eddington tensor in the implicit moment update.  For the
+ * faces normal to axis a (0 = x, 1 = y, 2 = z),
+ *   C = sqrt(f_aa) c sqrt((1 - e^-tau_c) / tau_c),
+ *   tau_c = (10 h kappa_R)^2 / (2 f_aa),
+ * tau_c formed per cell with that cell's f_aa and kappa_R and averaged over
+ * the face's two cells (the paper's rule between cells of one refinement
+ * level; the grid is uniform).  Readings: the face's free-streaming factor
+ * is the larger of its two cells' sqrt(f_aa) (left- and right-going speeds
+ * are -C and +C); a face on the domain boundary takes its one cell's values;
+ * f_aa <= 0 gives tau_c = inf and C's cell factor 0, kappa_R = 0 gives
+ * tau_c = 0 and the correction 1.  FP32: below tau_c = 1/4 the correction
+ * comes from the ray march's thin-segment cubic (no cancellation), above it
+ * from the hardware exponential; quotients are fast (a few ulp), so the
+ * result is within a few 1e-7 relative of the exact formula.
+ * grid: cells and h (block is ignored); f: [6][nz][ny][nx] as vet_closure
+ * writes it (only component a is read); kappa_R: [nz][ny][nx], rho kappa_R
+ * per unit length; c > 0; C_out: [nz][ny][nx+1] for a = 0, [nz][ny+1][nx]
+ * for a = 1, [nz+1][ny][nx] for a = 2 (face (x, y, z) lies on the low side
+ * of cell (x, y, z)).  All device memory, caller-owned; work is enqueued on
+ * `stream`.  VET_EINVAL for a bad grid, axis or c, or a missing or host
+ * pointer; VET_ECUDA for a failed launch.  Needs no context.
+ * ---------------------------------------------------------------------- */
+vet_status vet_hlle_wavespeed(const vet_grid *grid, const float *f, const float *kappa_R, double c, int axis,
+                              float *C_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * An entry point that allocates nothing (the paper has no counterpart; it
  * exists for callers of this library, not for the method).
  *

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libvet.so")
 SOURCES = ["vet_host.cu", "vet_kernels.cu", "vet_noalloc.cu", "vet_cnn.cu", "vet_cnn_tc.cu", "vet_learned.cu",
-           "vet_local.cu", "vet_point.cu", "vet_reuse.cu"]
+           "vet_local.cu", "vet_point.cu", "vet_reuse.cu", "vet_hlle.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
 

@@ -1,6 +1,7 @@
 // peaks.cu -- per-SM issue rates of the units the closure's kernels lean on,
 // measured on the GPU itself: MUFU ex2 (the exponential of every segment),
-// FP32 FMA, packed f32x2 FMA, and shared-memory loads of 8 and 16 bytes.
+// FP32 FMA, packed f32x2 FMA, shared-memory loads of 8 and 16 bytes, and the
+// cell pass's paired segment step on its own.
 //
 // One CTA of 1024 threads per SM runs independent dependency chains long
 // enough that only the unit's throughput limits them; the CTA reads clock64
@@ -123,6 +124,51 @@ __global__ void __launch_bounds__(kThreads, 1) lds_kernel(int iters, long long *
   record(t0, t1, cycles, s, out);
 }
 
+// The cell pass's paired segment step in isolation: a 16-byte load of a
+// (kappa, kappa', S, S') tile entry at an event's offset, the scaled optical
+// depths (f32x2), two ex2, the thin-segment cubic (f32x2), and one f32x2 FMA
+// on per-lane selected operands, per thread one ray pair marching through a
+// synthetic tile with an event list in shared memory.  Reports the clocks one
+// SM sub-partition spends per warp step (a ceiling on the march's rate).
+__global__ void __launch_bounds__(kThreads, 1) step_kernel(int iters, long long *cycles, float *out) {
+  extern __shared__ __align__(16) float4 tile[];  // 2048 entries, then 64 events
+  float2 *ev = reinterpret_cast<float2 *>(tile + 2048);
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+    tile[i] = make_float4(0.1f + 0.3f * (i & 7), 0.2f + 0.4f * (i % 5), 1.f + (i & 3), 2.f);
+  for (int i = threadIdx.x; i < 64; i += blockDim.x)
+    ev[i] = make_float2(-0.5f - 0.01f * i, __int_as_float(((i * 37) % 61 - 30) * 16));
+  __syncthreads();
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(tile) + 16u * (1024u + (threadIdx.x & 255u));
+  float2 I = make_float2(0.f, 1.f);
+  const float q3 = 8.70478970381660493e-03f, q2 = 5.53004379372010468e-02f, q1 = 2.40211763951330648e-01f,
+              q0 = 6.93147011611337405e-01f, thr = -0.36067376022224085f;
+  const long long t0 = clock64();
+  for (int s = 0; s < iters; s += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 v = ev[(s + u) & 63];
+      float4 q;
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                   : "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
+                   : "r"(base + (uint32_t)__float_as_int(v.y)));
+      const float2 Y = __fmul2_rn(make_float2(q.x, q.y), make_float2(v.x, v.x));
+      float e1, e2;
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(Y.x));
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(Y.y));
+      float2 p = __ffma2_rn(make_float2(q3, q3), Y, make_float2(q2, q2));
+      p = __ffma2_rn(p, Y, make_float2(q1, q1));
+      p = __ffma2_rn(p, Y, make_float2(q0, q0));
+      const float2 n = __fmul2_rn(p, Y);
+      const bool t1 = Y.x > thr, t2 = Y.y > thr;
+      I = __ffma2_rn(__fadd2_rn(I, make_float2(-q.z, -q.w)), make_float2(t1 ? n.x : e1, t2 ? n.y : e2),
+                     make_float2(t1 ? I.x : q.z, t2 ? I.y : q.w));
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  record(t0, t1, cycles, I.x + I.y, out);
+}
+
 template <typename K>
 double per_sm_rate(K kernel, int nsm, int iters, size_t smem, double units_per_thread_iter) {
   long long *d_cycles = nullptr;
@@ -159,10 +205,13 @@ int main() {
   const double ffma2 = per_sm_rate(ffma2_kernel, nsm, iters, one_per_sm, 2.0 * kChains);
   const double lds8 = per_sm_rate(lds_kernel<8>, nsm, iters, one_per_sm, 8.0 * kChains);
   const double lds16 = per_sm_rate(lds_kernel<16>, nsm, iters, one_per_sm, 16.0 * kChains);
+  // warp steps per SM clock -> SM sub-partition clocks per warp step
+  const double steps = per_sm_rate(step_kernel, nsm, iters, one_per_sm, 1.0 / 32.0);
+  const double step_clk = steps > 0 ? 4.0 / steps : -1.0;
   std::printf(
       "{\"device\": \"%s\", \"sms\": %d, \"ex2_per_clk_per_sm\": %.2f, \"ffma_lanes_per_clk_per_sm\": %.2f, "
       "\"ffma2_lanes_per_clk_per_sm\": %.2f, \"lds64_bytes_per_clk_per_sm\": %.2f, "
-      "\"lds128_bytes_per_clk_per_sm\": %.2f}\n",
-      p.name, nsm, ex2, ffma, ffma2, lds8, lds16);
-  return (ex2 > 0 && ffma > 0 && ffma2 > 0 && lds8 > 0 && lds16 > 0) ? 0 : 1;
+      "\"lds128_bytes_per_clk_per_sm\": %.2f, \"march_step_clk_per_smsp\": %.2f}\n",
+      p.name, nsm, ex2, ffma, ffma2, lds8, lds16, step_clk);
+  return (ex2 > 0 && ffma > 0 && ffma2 > 0 && lds8 > 0 && lds16 > 0 && step_clk > 0) ? 0 : 1;
 }

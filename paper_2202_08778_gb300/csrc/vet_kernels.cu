@@ -48,9 +48,7 @@ template <typename R> using vec2_t = typename Vec2<R>::T;
 // where a cubic suffices (a quartic on x < 1/2 costs one more fused
 // multiply-add per segment: 8% of the cell pass).  FP64: expm1 and exp2 of
 // the CUDA math library in the same two forms, thin for x < 1/2.
-constexpr float kQ3 = 8.70478970381660493e-03f, kQ2 = 5.53004379372010468e-02f, kQ1 = 2.40211763951330648e-01f,
-                kQ0 = 6.93147011611337405e-01f;
-constexpr float kThinY = -0.36067376022224085f;  // x < 1/4
+constexpr float kQ3 = kThinQ3, kQ2 = kThinQ2, kQ1 = kThinQ1, kQ0 = kThinQ0;  // vet_internal.h
 __device__ __forceinline__ float seg_weight(float y, bool &thin) {
   float e;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));

@@ -34,7 +34,7 @@ EXPORTS = (
     "vet_model_get_grads", "vet_model_features", "vet_model_forward", "vet_model_backward", "vet_model_step",
     "vet_closure_learned", "vet_model_last_timing", "vet_model_last_indicator", "vet_model_last_error",
     "vet_local_closure", "vet_point_source", "vet_field_change", "vet_reuse_decision", "vet_model_save",
-    "vet_model_load",
+    "vet_model_load", "vet_hlle_wavespeed",
 )
 
 #: functions whose return value is not a vet_status
@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True):
         lib.vet_closure_learned.argtypes = [vp, vp, vp, vp, vp, vp, f, vp, vp, ip, vp]
         lib.vet_model_last_timing.argtypes = [vp, ctypes.POINTER(f)]
         lib.vet_model_last_indicator.argtypes = [vp, vp, vp]
+        lib.vet_hlle_wavespeed.argtypes = [ctypes.POINTER(_Grid), vp, vp, ctypes.c_double, i, vp, vp]
         lib.vet_model_save.argtypes = [vp, ctypes.c_char_p]
         lib.vet_model_load.argtypes = [vp, ctypes.c_char_p]
         lib.vet_model_last_error.argtypes = [vp]
@@ -353,6 +354,25 @@ def field_change(shape, block: int, h: float, kappa, S, kappa_ref, S_ref, out, s
     if st != VET_OK:
         raise VetError(st, "vet_field_change")
     return out
+
+
+def hlle_wavespeed(shape, h: float, f, kappa_R, C_out, axis: int, c: float = 1.0, stream=None):
+    """vet_hlle_wavespeed: corrected HLLE wavespeeds of the faces normal to
+    `axis` (0 = x) of a grid of `shape` = (nz, ny, nx) cells of edge h, from
+    f [6][cells] and kappa_R [cells] (device); C_out has one more point along
+    the axis (see include/vet.h)."""
+    lib = load()
+    nz, ny, nx = (int(v) for v in shape)
+    n = nz * ny * nx
+    ext = [nz, ny, nx]
+    ext[2 - int(axis)] += 1
+    g = _Grid(nx, ny, nz, 1, float(h))
+    st = lib.vet_hlle_wavespeed(ctypes.byref(g), _ptr(f, np.float32, 6 * n, "f"), _ptr(kappa_R, np.float32, n, "kappa_R"),
+                                float(c), int(axis), _ptr(C_out, np.float32, int(np.prod(ext)), "C_out"),
+                                _stream(stream))
+    if st != VET_OK:
+        raise VetError(st, "vet_hlle_wavespeed")
+    return C_out
 
 
 def reuse_decision(change, age: int, first: bool, tol_tau: float, tol_S: float, max_age: int) -> bool:
