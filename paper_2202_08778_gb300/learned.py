@@ -115,12 +115,91 @@ def evaluate(model, data, shape, B: int, h: float, block_edge: int):
             "eddington_mean": float(ee.mean()), "blocks_below_1e-2": float(np.mean(blocks_ok))}
 
 
+def accepted_on_field(model, n: int = 256, B: int = 16, nside: int = 4, seed: int = 3, threshold: float = 1e-2):
+    """The learned closure with fallback on a seeded n^3 lognormal field
+    (E from the exact closure, as in the benchmark): blocks the indicator
+    keeps, their largest |f - f_traced|, and the times of the plain and the
+    learned closures (ms, medians of three)."""
+    import statistics
+
+    import torch
+
+    p = synth.lognormal_problem(n=n, B=B, nside=nside, seed=seed)
+    ctx = vet.Context(p["kappa"].shape, B, p["h"], nside, p["q"])
+    k = torch.from_numpy(np.ascontiguousarray(p["kappa"].astype(np.float32))).cuda()
+    S = torch.from_numpy(np.ascontiguousarray(p["S"].astype(np.float32))).cuda()
+    N = n ** 3
+    nblk = N // B ** 3
+    f_plain = torch.empty(6 * N, device="cuda")
+    M = torch.empty(10 * N, device="cuda")
+    ctx.closure(k, S, None, f_plain, M)
+    E = M[:N].clone()
+    del M
+    ctx.set_timing(True)
+    plain = []
+    for _ in range(3):
+        ctx.closure(k, S, None, f_plain)
+        plain.append(ctx.last_timing()[3])
+    ctx.set_timing(False)
+    f = torch.empty(6 * N, device="cuda")
+    flags = torch.zeros(nblk, dtype=torch.int32, device="cuda")
+    ts = []
+    nfb = 0
+    for _ in range(3):
+        nfb = model.closure(ctx, k, S, E, f, threshold=threshold, block_flags=flags)
+        ts.append(model.last_timing()[2])
+    ctx.sync()
+    kept = ~flags.bool()
+    err = (f - f_plain).abs().view(6, -1).amax(0)
+    nb = n // B
+    eb = err.view(nb, B, nb, B, nb, B).amax(dim=(1, 3, 5)).reshape(-1)
+    return {"blocks": nblk, "kept": int(kept.sum()), "kept_fraction": float(kept.double().mean()),
+            "kept_max_abs_df": float(eb[kept].max()) if bool(kept.any()) else 0.0,
+            "plain_ms": statistics.median(plain), "learned_ms": statistics.median(ts), "fallback_blocks": nfb}
+
+
+def curve(counts=(64, 512, 2000), steps_per_snapshot: float = 10.0, min_steps: int = 1500, batch: int = 4,
+          nt: int = 64, B: int = 16, nside: int = 4):
+    """Accuracy of the learned closure against the amount of training data:
+    for each snapshot count, train from scratch on the first that many of
+    2000 seeded 64^3 snapshots (seeds 10000..11999, labelled by the exact
+    closure) and report held-out errors (16 snapshots, seeds 20000..20015)
+    and the blocks the indicator keeps at 1e-2 on the 256^3 field of seed 3."""
+    import time
+
+    import torch
+
+    ctx_t = vet.Context((nt,) * 3, B, 1.0 / nt, nside, synth.rotation_quaternion(10000))
+    t0 = time.perf_counter()
+    data = snapshots(ctx_t, range(10000, 10000 + max(counts)), nt, B, nside)
+    held = snapshots(ctx_t, range(20000, 20016), nt, B, nside)
+    t_data = time.perf_counter() - t0
+    out = []
+    for c in counts:
+        sub = tuple(x[:c] for x in data)
+        steps = max(min_steps, int(steps_per_snapshot * c))
+        model = vet.Model()
+        model.set_params(init_params(32, seed=0))
+        t0 = time.perf_counter()
+        losses = train(model, sub, (nt,) * 3, B, 1.0 / nt, steps, batch=batch)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        res = {"snapshots": c, "steps": steps, "batch": batch, "train_seconds": t_train, "final_loss": losses[-1],
+               "held_out": evaluate(model, held, (nt,) * 3, B, 1.0 / nt, B),
+               "field256_seed3": accepted_on_field(model)}
+        out.append(res)
+        print(res, flush=True)
+    return {"data_seconds": t_data, "runs": out}
+
+
 def main(argv=None):
     """Without --train: run the learned closure (network only, no fallback) on
     a seeded n^3 lognormal field after the exact closure that supplies E and
     print the device timings (untrained network: cost, not accuracy).
     With --train: train the network on 64^3 snapshots of the lognormal
-    generator labelled by the exact closure and print held-out errors."""
+    generator labelled by the exact closure and print held-out errors.
+    With --curve: the same for 64, 512 and 2000 snapshots, with the blocks
+    the indicator keeps on the 256^3 field of seed 3 (one JSON line)."""
     import argparse
     import time
 
@@ -136,7 +215,14 @@ def main(argv=None):
     ap.add_argument("--snapshots", type=int, default=512)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--curve", action="store_true",
+                    help="train on 64, 512 and 2000 snapshots and report errors and kept blocks")
     a = ap.parse_args(argv)
+    if a.curve:
+        import json
+
+        print(json.dumps(curve(batch=a.batch)))
+        return
     if a.train:
         nt = 64
         ctx_t = vet.Context((nt,) * 3, a.block, 1.0 / nt, a.nside, synth.rotation_quaternion(10000))
