@@ -52,16 +52,21 @@ def workload():
                "seed": 2, "boundary": "vacuum", "l2": "flushed between timed steps (256 MiB write)"}
 
 
-def kernel_source_digest(path: str) -> str:
-    """SHA-256 of a CUDA source with its comments and blank lines removed, so
-    that a comment edit does not count as a kernel change."""
+def kernel_source_digest(paths) -> str:
+    """SHA-256 of CUDA sources (one path or a list: the kernel's file and the
+    headers that fix its constants and layouts) with comments and blank lines
+    removed, so that a comment edit does not count as a kernel change."""
     import hashlib
     import re
 
-    src = open(path, encoding="utf-8").read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    src = re.sub(r"//[^\n]*", "", src)
-    lines = [ln.rstrip() for ln in src.splitlines() if ln.strip()]
+    if isinstance(paths, str):
+        paths = [paths]
+    lines = []
+    for path in paths:
+        src = open(path, encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        lines += [ln.rstrip() for ln in src.splitlines() if ln.strip()]
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
@@ -70,7 +75,8 @@ def measured_traffic():
     if the kernel source changed since the counters were taken."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "cell_pass_lognormal128_traffic.json")))
-        digest = kernel_source_digest(os.path.join(ROOT, rec["source"]))
+        src = rec["source"] if isinstance(rec["source"], list) else [rec["source"]]
+        digest = kernel_source_digest([os.path.join(ROOT, x) for x in src])
     except (OSError, ValueError, KeyError):
         return None
     if digest != rec.get("kernel_source_digest"):

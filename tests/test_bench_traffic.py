@@ -30,3 +30,12 @@ def test_record_is_consistent():
     rec = json.load(open(os.path.join(ROOT, "profiles", "cell_pass_lognormal128_traffic.json")))
     assert rec["bytes_per_launch"] == rec["dram_read_bytes"] + rec["dram_write_bytes"]
     assert len(rec["kernel_source_digest"]) == 64
+
+
+def test_digest_covers_every_listed_source(tmp_path):
+    a, h, h2 = tmp_path / "a.cu", tmp_path / "a.h", tmp_path / "a2.h"
+    a.write_text(SRC)
+    h.write_text("constexpr float kC = 0.5f;  // a constant\n")
+    h2.write_text("constexpr float kC = 0.25f;\n")
+    assert bench.kernel_source_digest([str(a), str(h)]) != bench.kernel_source_digest([str(a), str(h2)])
+    assert bench.kernel_source_digest([str(a)]) == bench.kernel_source_digest(str(a))
