@@ -734,11 +734,27 @@ __device__ __forceinline__ float2 step_pair(uint32_t ta, float len, float2 I) {
 // at t1.  The warp runs from its largest `last` down to event 0; a lane
 // whose own ray is shorter reads the identity entry id (kappa = 0: the thin
 // form returns I exactly) until the index reaches its `last`; below the
-// warp's smallest `last` every lane marches and events are read in 16-byte
-// pairs.
+// warp's smallest `last` every lane marches.  After one step to an odd
+// index, events are read in 16-byte pairs, four steps a trip, in both
+// phases (the guarded phase while four or more of its steps remain).
 __device__ __forceinline__ float2 march_pair(uint32_t t1, uint32_t id, uint32_t ev, int last, float2 I) {
   int e = __reduce_max_sync(0xffffffffu, last);
   const int wmin = __reduce_min_sync(0xffffffffu, last);
+  if (e - wmin >= 4) {  // guarded steps four at a time on 16-byte event pairs
+    if (!(e & 1)) {
+      const float2 v = lds_f2(ev + 8 * e);
+      I = step_pair(e <= last ? t1 + 2 * (int)__float_as_uint(v.y) : id, v.x, I);
+      --e;
+    }
+    for (; e - wmin >= 4; e -= 4) {  // e - 3 > wmin >= 0
+      const float4 a = lds_f4(ev + 8 * (e - 1));
+      const float4 b = lds_f4(ev + 8 * (e - 3));
+      I = step_pair(e <= last ? t1 + 2 * (int)__float_as_uint(a.w) : id, a.z, I);
+      I = step_pair(e - 1 <= last ? t1 + 2 * (int)__float_as_uint(a.y) : id, a.x, I);
+      I = step_pair(e - 2 <= last ? t1 + 2 * (int)__float_as_uint(b.w) : id, b.z, I);
+      I = step_pair(e - 3 <= last ? t1 + 2 * (int)__float_as_uint(b.y) : id, b.x, I);
+    }
+  }
   for (; e > wmin; --e) {
     const float2 v = lds_f2(ev + 8 * e);
     I = step_pair(e <= last ? t1 + 2 * (int)__float_as_uint(v.y) : id, v.x, I);
@@ -943,7 +959,10 @@ __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
   unsigned char *ring = smem + align16(sizeof(float4) * (size_t)ts.elems);
   const uint32_t ring_s = smem_u32(ring);
   const size_t stage_bytes = (size_t)dt * CS.bytes;
-  const int item = blockIdx.x / parts, part = blockIdx.x - item * parts;
+  // the parts of a block are neighbours in launch order, so that the second
+  // finds the block's staged faces still in L2 (running every block's part 1
+  // before any part 0 read them from DRAM twice: 736 instead of 361 MB)
+  const int item = (int)blockIdx.x / parts, part = parts - 1 - ((int)blockIdx.x - item * parts);
   const int blk = block_list ? block_list[item] : item;
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
   constexpr int nwarps = NT / 32;
@@ -980,7 +999,13 @@ __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
   const int qb = q >> 5, ln = q & 31;
   const int cx = 4 * (qb % (B / 4)) + (ln & 3);
   const int cy = 4 * ((qb / (B / 4)) % (B / 4)) + ((ln >> 2) & 3);
-  const int cz = 2 * (qb / (B2 / 16)) + (ln >> 4);
+  // layer pair lp holds z = 2 lp, 2 lp + 1 of the lower half; with two parts
+  // of a 16^3 block, part 0 takes layer pairs 0 and 3 and part 1 takes 1 and
+  // 2 (85e3 and 89e3 warp steps over 192 directions, where z-order parts
+  // differ by 15%), so that the CTAs of a wave carry about equal work
+  int lp = qb / (B2 / 16);
+  if (B == 16 && parts == 2) lp = (0x2130 >> (4 * lp)) & 15;
+  const int cz = 2 * lp + (ln >> 4);
   const int mx = B - 1 - cx, my = B - 1 - cy, mz = B - 1 - cz;  // the mirror cell
   const uint32_t tile_s = smem_u32(tile);
   const uint32_t t1 = tile_s + 16u * (uint32_t)(cx + ts.sy * cy + ts.sz * cz);

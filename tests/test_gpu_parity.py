@@ -105,7 +105,8 @@ NEAR_PLANE_Q = np.array([np.sqrt(0.5), 1 / np.sqrt(10.0), 1 / np.sqrt(3.0), 0.2]
 
 
 @pytest.mark.parametrize("case", ["blob32", "lognormal48", "cloud", "ragged", "tiny_blocks", "unrotated8",
-                                  "unrotated16", "near_plane8", "near_plane16"])
+                                  "unrotated16", "near_plane8", "near_plane16", "single_block16", "vacuum",
+                                  "opaque", "block12"])
 def test_fp32_closure_matches_oracle(ora, case):
     """The unrotated cases hold directions with an exactly zero component (the
     HEALPix equator ring, n_z = 0), where a direction and its antipode both
@@ -130,6 +131,19 @@ def test_fp32_closure_matches_oracle(ora, case):
         p = synth.lognormal_problem(n=48, B=16, nside=4, seed=2)
     elif case == "cloud":
         p = synth.cloud_problem(nx=64, ny=32, nz=32, B=16, nside=4, seed=3)
+    elif case == "single_block16":  # one block: no face-pass level, every entry from the boundary
+        p = synth.lognormal_problem(n=16, B=16, nside=4, seed=27)
+        Ib = np.random.default_rng(27).uniform(0, 0.5, (6, 192))
+    elif case == "vacuum":  # kappa = 0: every ray carries its boundary value unchanged
+        p = synth.lognormal_problem(shape=(16, 32, 48), B=16, nside=4, seed=28)
+        p["kappa"] = np.zeros_like(p["kappa"])
+        Ib = np.random.default_rng(28).uniform(0, 0.5, (6, 192))
+    elif case == "opaque":  # 1e4 optical depths per cell: I = S to rounding
+        p = synth.lognormal_problem(n=32, B=8, nside=2, seed=29)
+        p["kappa"] = np.full_like(p["kappa"], 1e4 / p["h"])
+        Ib = np.random.default_rng(29).uniform(0, 0.5, (6, 48))
+    elif case == "block12":  # a block edge the mirrored kernels do not take (generic passes)
+        p = synth.lognormal_problem(shape=(24, 36, 48), B=12, nside=2, seed=30)
     elif case == "ragged":
         p = synth.lognormal_problem(shape=(24, 16, 40), B=8, nside=2, seed=22)
         Ib = np.random.default_rng(22).uniform(0, 0.5, (6, 48))
@@ -144,6 +158,8 @@ def test_fp32_closure_matches_oracle(ora, case):
     f_ref, M_ref, I_ref, _ = ora.vet_closure(host_in[0], host_in[1], dirs, p["B"], p["h"], host_in[2])
     I = _gpu_trace(ctx, dev_in, I_ref[0].size, np.float32)
     assert rel_err(I, I_ref.reshape(ctx.N, -1)) < RTOL32
+    if case == "opaque":  # the last half cell alone is 5e3 optical depths: I is the cell's S exactly
+        assert np.array_equal(I, np.broadcast_to(host_in[1].astype(np.float32).ravel(), I.shape))
     f, M = _gpu_closure(ctx, dev_in, I_ref[0].size, np.float32)
     eE, eFP = moment_errors(M, M_ref)
     assert eE < RTOL32 and eFP < RTOL32, (eE, eFP)
