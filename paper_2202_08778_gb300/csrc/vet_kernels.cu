@@ -729,6 +729,27 @@ __device__ __forceinline__ float2 step_pair(uint32_t ta, float len, float2 I) {
                     make_float2(t1 ? I.x : q.z, t2 ? I.y : q.w));
 }
 
+// The step of a lane that may be idle: an idle lane loads nothing and
+// steps on zeros (kappa = 0: the thin form returns I exactly), so that a
+// quarter-warp with no active lane issues no shared-memory wavefront.
+__device__ __forceinline__ float2 step_pair_g(bool act, uint32_t ta, float len, float2 I) {
+  float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+  asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n @p ld.shared.v4.f32 {%0, %1, %2, %3}, [%5];\n}\n"
+               : "+f"(q.x), "+f"(q.y), "+f"(q.z), "+f"(q.w)
+               : "r"((uint32_t)act), "r"(ta));
+  const float2 Y = __fmul2_rn(make_float2(q.x, q.y), make_float2(len, len));
+  float e1, e2;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(Y.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(Y.y));
+  float2 p = __ffma2_rn(make_float2(kQ3, kQ3), Y, make_float2(kQ2, kQ2));
+  p = __ffma2_rn(p, Y, make_float2(kQ1, kQ1));
+  p = __ffma2_rn(p, Y, make_float2(kQ0, kQ0));
+  const float2 n = __fmul2_rn(p, Y);
+  const bool t1 = Y.x > kThinY, t2 = Y.y > kThinY;
+  return __ffma2_rn(__fadd2_rn(I, neg2(make_float2(q.z, q.w))), make_float2(t1 ? n.x : e1, t2 ? n.y : e2),
+                    make_float2(t1 ? I.x : q.z, t2 ? I.y : q.w));
+}
+
 // March of a mirrored ray pair: events at shared address ev (8 bytes each:
 // scaled length, byte offset for 8-byte tile entries), primary start entry
 // at t1.  The warp runs from its largest `last` down to event 0; a lane
@@ -1306,8 +1327,10 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     float2 I = make_float2(face_value<float>(fin1, g.fstride, B, ae, lb, lc, kb, kc, wb, wc),
                            face_value<float>(fin2, g.fstride, B, ae, lb, lc, kb, kc, wb, wc));
     if (!act) last = -1;
-    // lockstep aligned at the downwind end, as in the unpaired face pass;
-    // a lane whose own ray is shorter reads the identity entry
+    // lockstep aligned at the downwind end, as in the unpaired face pass; a
+    // lane whose own ray is shorter steps on zeros without a load (a
+    // quarter-warp of such lanes costs no shared-memory wavefront); events
+    // four at a time in 16-byte pairs
     const int wl = __reduce_max_sync(0xffffffffu, last);
     if (wl >= 0) {
       const int c0 = T.h->sgn[0] > 0 ? L0 - 1 : B - L0;
@@ -1318,13 +1341,21 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
       int e = wl;
       if (!(e & 1)) {  // to an odd index: event pairs (e - 1, e) are 16-byte aligned
         const float2 v = lds_f2(ev + 8 * e);
-        I = step_pair(e <= last ? tb + 2 * (int)__float_as_uint(v.y) : id_s, v.x, I);
+        I = step_pair_g(e <= last, tb + 2 * (int)__float_as_uint(v.y), v.x, I);
         --e;
       }
-      for (; e >= 1; e -= 2) {
+      for (; e >= 3; e -= 4) {
         const float4 v = lds_f4(ev + 8 * (e - 1));
-        I = step_pair(e <= last ? tb + 2 * (int)__float_as_uint(v.w) : id_s, v.z, I);
-        I = step_pair(e - 1 <= last ? tb + 2 * (int)__float_as_uint(v.y) : id_s, v.x, I);
+        const float4 u = lds_f4(ev + 8 * (e - 3));
+        I = step_pair_g(e <= last, tb + 2 * (int)__float_as_uint(v.w), v.z, I);
+        I = step_pair_g(e - 1 <= last, tb + 2 * (int)__float_as_uint(v.y), v.x, I);
+        I = step_pair_g(e - 2 <= last, tb + 2 * (int)__float_as_uint(u.w), u.z, I);
+        I = step_pair_g(e - 3 <= last, tb + 2 * (int)__float_as_uint(u.y), u.x, I);
+      }
+      if (e == 1) {
+        const float4 v = lds_f4(ev);
+        I = step_pair_g(1 <= last, tb + 2 * (int)__float_as_uint(v.w), v.z, I);
+        I = step_pair_g(0 <= last, tb + 2 * (int)__float_as_uint(v.y), v.x, I);
       }
     }
     if (act) {
