@@ -159,7 +159,7 @@ def accepted_on_field(model, n: int = 256, B: int = 16, nside: int = 4, seed: in
 
 
 def curve(counts=(64, 512, 2000), steps_per_snapshot: float = 10.0, min_steps: int = 1500, batch: int = 4,
-          nt: int = 64, B: int = 16, nside: int = 4):
+          nt: int = 64, B: int = 16, nside: int = 4, lr_max: float = 2e-3):
     """Accuracy of the learned closure against the amount of training data:
     for each snapshot count, train from scratch on the first that many of
     2000 seeded 64^3 snapshots (seeds 10000..11999, labelled by the exact
@@ -181,10 +181,11 @@ def curve(counts=(64, 512, 2000), steps_per_snapshot: float = 10.0, min_steps: i
         model = vet.Model()
         model.set_params(init_params(32, seed=0))
         t0 = time.perf_counter()
-        losses = train(model, sub, (nt,) * 3, B, 1.0 / nt, steps, batch=batch)
+        losses = train(model, sub, (nt,) * 3, B, 1.0 / nt, steps, batch=batch, lr_max=lr_max)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
-        res = {"snapshots": c, "steps": steps, "batch": batch, "train_seconds": t_train, "final_loss": losses[-1],
+        res = {"snapshots": c, "steps": steps, "batch": batch, "lr_max": lr_max, "train_seconds": t_train,
+               "final_loss": losses[-1],
                "held_out": evaluate(model, held, (nt,) * 3, B, 1.0 / nt, B),
                "field256_seed3": accepted_on_field(model)}
         out.append(res)
@@ -217,11 +218,14 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--curve", action="store_true",
                     help="train on 64, 512 and 2000 snapshots and report errors and kept blocks")
+    ap.add_argument("--counts", type=str, default="64,512,2000", help="snapshot counts of --curve")
+    ap.add_argument("--lr", type=float, default=2e-3, help="peak learning rate of the cosine schedule (--curve)")
     a = ap.parse_args(argv)
     if a.curve:
         import json
 
-        print(json.dumps(curve(batch=a.batch)))
+        counts = tuple(int(c) for c in a.counts.split(","))
+        print(json.dumps(curve(counts=counts, batch=a.batch, lr_max=a.lr)))
         return
     if a.train:
         nt = 64
