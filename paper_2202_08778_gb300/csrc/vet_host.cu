@@ -43,6 +43,7 @@ struct vet_ctx {
   long long spin = 0;            // polls per device-side wait
   void *d_stage = nullptr;       // staging of host-pointer arguments
   size_t stage_bytes = 0;
+  vet::TailSplit split;          // scratch of the cell pass's tail split (none: split.nsm = 0)
   long long cell_segs = 0, face_segs = 0;
   int ob[9] = {0};                // octant ranges of the internal direction order
   int face_group = vet::kFaceGroup;  // directions per face-pass item (tunable)
@@ -97,6 +98,8 @@ void free_ctx(vet_ctx *c) {
   cudaFree(c->d_bnd);
   cudaFree(c->d_status);
   cudaFree(c->d_stage);
+  cudaFree(c->split.part);
+  cudaFree(c->split.count);
   delete c;
 }
 
@@ -140,6 +143,41 @@ vet_status build_schedule(vet_ctx *c, int group) {
   c->face_group = group;
   ++c->tuning_gen;  // a batch graph captured with the old schedule must not replay
   return VET_OK;
+}
+
+// Scratch of the paired cell pass's tail split for the whole grid (the
+// largest plan over the direction tiles the tuning can pick); the split is
+// left off when the pass is not paired or the plan does not split.
+vet_status enable_tail_split(vet_ctx *c) {
+  if (!c->dims.paired || c->split.part) return VET_OK;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->cfg.device) != cudaSuccess) {
+    cudaGetLastError();
+    return VET_OK;
+  }
+  vet::TailPlan best;
+  for (int dt = 2; dt <= vet::kMaxTune; dt += 2) {
+    const vet::TailPlan p = vet::plan_tail_split(c->grid.block, c->nblk, nsm, (c->N + dt - 1) / dt);
+    if (p.part_bytes > best.part_bytes) best = p;
+  }
+  c->split.nsm = nsm;
+  if (best.k <= 1) return VET_OK;  // trace-mode splits need no scratch
+  cudaError_t e;
+  if ((e = cudaMalloc((void **)&c->split.part, best.part_bytes))) return cuda_err(c, e, "cudaMalloc(tail split)");
+  if ((e = cudaMalloc((void **)&c->split.count, sizeof(int) * best.slots)))
+    return cuda_err(c, e, "cudaMalloc(tail split counts)");
+  if ((e = cudaMemset(c->split.count, 0, sizeof(int) * best.slots))) return cuda_err(c, e, "cudaMemset(tail split)");
+  c->split.part_bytes = best.part_bytes;
+  c->split.slots = best.slots;
+  return VET_OK;
+}
+
+// Off for grids of a batch, whose closures share the GPU: a lone grid's last
+// wave leaves SMs idle, a batch's does not.
+void disable_tail_split(vet_ctx *c) {
+  cudaFree(c->split.part);
+  cudaFree(c->split.count);
+  c->split = vet::TailSplit();
 }
 
 template <typename R>
@@ -236,7 +274,7 @@ vet_status build_context(vet_ctx *c) {
   if ((e = cudaMemcpy(c->d_coef, coef.data(), sizeof(R) * coef.size(), cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload coefficients");
   if ((e = vet::prepare_kernels())) return cuda_err(c, e, "cudaFuncSetAttribute");
-  return VET_OK;
+  return enable_tail_split(c);
 }
 
 bool is_device_ptr(const void *p) {
@@ -361,6 +399,8 @@ vet_status check_status(vet_ctx *c) {
   if (e) return cuda_err(c, e, "status read");
   if (st) {
     cudaMemset(c->d_status, 0, sizeof(int));
+    // a share that gave up may not have counted itself
+    if (c->split.count) cudaMemset(c->split.count, 0, sizeof(int) * c->split.slots);
     return set_err(c, VET_ETIMEOUT,
                    "a device-side wait gave up (status bits " + std::to_string(st) + "); outputs are incomplete");
   }
@@ -427,7 +467,8 @@ vet_status do_trace(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *I_ou
   if ((s = mark(c, 1, st))) return s;
   cudaError_t e = vet::launch_cell_pass<R>(c->dims, 1, din[0], din[1], (const unsigned char *)c->d_tpl,
                                            c->d_cell_order, (const R *)c->d_faces, (const R *)c->d_bnd, dout[0],
-                                           nullptr, nullptr, nullptr, nullptr, c->spin, c->d_status, st);
+                                           nullptr, nullptr, nullptr, nullptr, c->spin, c->d_status, st, nullptr, 0,
+                                           c->split.nsm ? &c->split : nullptr);
   if (e) return cuda_err(c, e, "cell pass launch");
   if ((s = mark(c, 2, st)) || (s = mark(c, 3, st))) return s;
   c->last_stream = st;
@@ -485,7 +526,7 @@ vet_status do_closure(vet_ctx *c, const R *kappa, const R *S, const R *Ib, R *f_
   R *Mdev = dout[1];
   e = vet::launch_cell_pass<R>(c->dims, 0, din[0], din[1], (const unsigned char *)c->d_tpl, c->d_cell_order,
                                (const R *)c->d_faces, (const R *)c->d_bnd, nullptr, Mdev, (R *)c->d_E, dout[0],
-                               c->d_emax, c->spin, c->d_status, st);
+                               c->d_emax, c->spin, c->d_status, st, nullptr, 0, c->split.nsm ? &c->split : nullptr);
   if (e) return cuda_err(c, e, "cell pass launch");
   if ((s = mark(c, 2, st))) return s;
   const R *E = Mdev ? Mdev : (const R *)c->d_E;
@@ -822,6 +863,7 @@ VET_API vet_status vet_batch_create(vet_batch **out, int n, const vet_grid *grid
       free_batch(b);
       return st;
     }
+    disable_tail_split(c);
     b->ctx.push_back(c);
   }
   DeviceGuard dg(b->device);

@@ -170,14 +170,44 @@ cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, con
                               const FaceItem *items, int nitems, int max_dirs, R *faces, const R *bnd,
                               long long spin, int *status, cudaStream_t st);
 
+// Split of the paired cell pass's last partial wave.  With `total` CTAs and
+// room for `wave` of them at once (SMs x CTAs per SM) the last wave holds
+// r = total mod wave CTAs and leaves the other slots idle for a whole CTA's
+// time; the last r CTAs' work is then cut into k shares of their direction
+// tiles (k CTAs each), so that the tail takes about ceil(k r / wave) / k of
+// a CTA's time.  The shares' partial moments meet in `part`
+// ([slot][share][28][threads] floats) and the last share of a slot to
+// finish (counted in `count`, which it resets) adds the others' and writes
+// the outputs.
+struct TailPlan {
+  int nfull = 0;          // CTAs that run whole (total - r)
+  int k = 1;              // shares per split work item (1: no split)
+  int slots = 0;          // r
+  size_t part_bytes = 0;  // scratch the moments of the shares need
+};
+TailPlan plan_tail_split(int B, int nblk, int nsm, int ntiles);
+
+// What the caller provides for the split: the SM count and the scratch
+// (part: part_bytes, count: slots zeroed ints).  part == nullptr: no split
+// of the moment passes (the trace needs no scratch).
+struct TailSplit {
+  int nsm = 0;
+  float *part = nullptr;
+  size_t part_bytes = 0;
+  int *count = nullptr;
+  int slots = 0;
+};
+
 // mode 0: moments + f (+ E for the floor rule); mode 1: write I_out.  The
 // directions are visited in cell_order.  With a block_list (device, nlist
-// block indices) only the cells of those blocks are computed.
+// block indices) only the cells of those blocks are computed.  `split`
+// (paired FP32 pass only; null: none) cuts the last partial wave, see
+// TailSplit; its part/count must hold the plan's slots.
 template <typename R>
 cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const unsigned char *tpl,
                              const int *cell_order, const R *faces, const R *bnd, R *I_out, R *M_out, R *E_out,
                              R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st,
-                             const int *block_list = nullptr, int nlist = 0);
+                             const int *block_list = nullptr, int nlist = 0, const TailSplit *split = nullptr);
 
 // The floor rule on the cells of the listed blocks.
 template <typename R>

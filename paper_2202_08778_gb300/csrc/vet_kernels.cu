@@ -965,7 +965,8 @@ __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
                      const int *__restrict__ order, const float *__restrict__ faces, const float *__restrict__ bnd,
                      float *__restrict__ I_out, float *__restrict__ M_out, float *__restrict__ E_out,
                      float *__restrict__ f_out, void *emax_bits, long long spin_limit, int *status,
-                     const int *__restrict__ block_list) {
+                     const int *__restrict__ block_list, int nfull, int ksplit, float *__restrict__ split_part,
+                     int *__restrict__ split_count) {
   constexpr int B = BC, B2 = B * B, NT = pair_threads(BC);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kPairStagesMax], empty[kPairStagesMax];
@@ -983,15 +984,24 @@ __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
   // the parts of a block are neighbours in launch order, so that the second
   // finds the block's staged faces still in L2 (running every block's part 1
   // before any part 0 read them from DRAM twice: 736 instead of 361 MB)
-  const int item = (int)blockIdx.x / parts, part = parts - 1 - ((int)blockIdx.x - item * parts);
+  // past nfull, ksplit consecutive CTAs share one work item (slot), each a
+  // contiguous run of its direction tiles (the tail split)
+  int cta = (int)blockIdx.x, share = 0, slot = -1;
+  if (ksplit > 1 && cta >= nfull) {
+    slot = (cta - nfull) / ksplit;
+    share = cta - nfull - slot * ksplit;
+    cta = nfull + slot;
+  }
+  const int item = cta / parts, part = parts - 1 - (cta - item * parts);
   const int blk = block_list ? block_list[item] : item;
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
   constexpr int nwarps = NT / 32;
-  const int ntiles = (g.ndir + dt - 1) / dt;
-  // producer state, meaningful in thread 0 only
+  const int ntiles_all = (g.ndir + dt - 1) / dt, nshares = slot >= 0 ? ksplit : 1;
+  const int tile0 = share * ntiles_all / nshares, ntiles = (share + 1) * ntiles_all / nshares - tile0;
+  // producer state, meaningful in thread 0 only; tiles counted from tile0
   int issued = 0, consumed = 0;
   auto issue_tile = [&](int t) {
-    const int s = t % nstage, d0 = t * dt, nd = min(dt, g.ndir - d0);
+    const int s = t % nstage, d0 = (tile0 + t) * dt, nd = min(dt, g.ndir - d0);
     unsigned char *buf = ring + (size_t)s * stage_bytes;
     mbar_expect_tx(&full[s], (uint32_t)(CS.bytes * nd));
     for (int j = 0; j < nd; ++j) {
@@ -1101,7 +1111,7 @@ __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
     }
     if (!mbar_wait_sleep_warp(full_s + 8 * st, ph, spin_limit, status, 2)) { ok = false; break; }
     if (threadIdx.x == 0) consumed = t + 1;
-    const int nd = min(dt, g.ndir - t * dt);
+    const int nd = min(dt, g.ndir - (tile0 + t) * dt);
     const uint32_t buf = ring_s + (uint32_t)(st * stage_bytes);
     for (int j = 0; j < nd; j += 2) {  // the antipodal pair (j, j + 1)
       const uint32_t sa = buf + (uint32_t)(CS.bytes * j), sb = sa + (uint32_t)CS.bytes;
@@ -1166,6 +1176,52 @@ __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
   if (threadIdx.x == 0) {
     for (int t = consumed; t < issued; ++t)
       if (!mbar_wait_sleep(full_s + 8 * (t % nstage), (uint32_t)((t / nstage) & 1), kDrainPolls)) atomicOr(status, 8);
+  }
+  if (MODE != 1 && slot >= 0) {
+    // one share of a split work item: its partial sums go to the slot's
+    // scratch, and the share that finishes last adds the others' (the
+    // compensated sums as compensated sums) and writes the outputs
+    constexpr int kVals = 28;
+    __shared__ int s_last;
+    float *mine = split_part + ((size_t)slot * ksplit + share) * kVals * NT + threadIdx.x;
+#pragma unroll
+    for (int m = 0; m < 10; ++m) {
+      mine[(2 * m) * NT] = mom[m].x;
+      mine[(2 * m + 1) * NT] = mom[m].y;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      mine[(20 + 2 * m) * NT] = nc[m].x;
+      mine[(21 + 2 * m) * NT] = nc[m].y;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(split_count + slot, 1) == ksplit - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const float2 one = make_float2(1.f, 1.f);
+    for (int r = 0; r < ksplit; ++r) {
+      if (r == share) continue;
+      const float *other = split_part + ((size_t)slot * ksplit + r) * kVals * NT + threadIdx.x;
+      float2 pm[10], pn[4];
+#pragma unroll
+      for (int m = 0; m < 10; ++m) pm[m] = make_float2(__ldcg(other + (2 * m) * NT), __ldcg(other + (2 * m + 1) * NT));
+#pragma unroll
+      for (int m = 0; m < 4; ++m) pn[m] = make_float2(__ldcg(other + (20 + 2 * m) * NT), __ldcg(other + (21 + 2 * m) * NT));
+      nc[0] = __fadd2_rn(nc[0], pn[0]);
+      kahan2(mom[0], nc[0], one, pm[0]);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        nc[1 + m] = __fadd2_rn(nc[1 + m], pn[1 + m]);
+        kahan2(mom[4 + m], nc[1 + m], one, pm[4 + m]);
+      }
+#pragma unroll
+      for (int m = 1; m < 4; ++m) mom[m] = __fadd2_rn(mom[m], pm[m]);
+#pragma unroll
+      for (int m = 7; m < 10; ++m) mom[m] = __fadd2_rn(mom[m], pm[m]);
+    }
+    if (threadIdx.x == 0) split_count[slot] = 0;  // ready for the next call
   }
   if (MODE != 1) {
     float emax = 0.f;
@@ -1560,26 +1616,69 @@ inline void pair_staging(int B, int want, int &dt, int &nstage) {
   }
 }
 
+}  // namespace
+
+TailPlan plan_tail_split(int B, int nblk, int nsm, int ntiles) {
+  TailPlan p;
+  if (B != 8 && B != 16) return p;
+  const int parts = B * B * B / 2 / pair_threads(B), total = nblk * parts;
+  p.nfull = total;
+  const int wave = nsm * pair_min_ctas(B);
+  if (nsm <= 0 || total < wave) return p;
+  const int r = total % wave;
+  if (r == 0) return p;
+  // tail time in CTA times, with each share's own start (tile load, first
+  // staging) counted as 3% of a CTA; split only for a gain above 5%
+  double best = 1.0;
+  for (int k : {2, 3, 4, 6, 8}) {
+    if (k > ntiles) break;
+    const double cost = (double)((k * r + wave - 1) / wave) / k + 0.03 * k;
+    if (cost < best - 0.05) {
+      best = cost;
+      p.k = k;
+    }
+  }
+  if (p.k == 1) return p;
+  p.nfull = total - r;
+  p.slots = r;
+  p.part_bytes = (size_t)r * p.k * 28 * pair_threads(B) * sizeof(float);
+  return p;
+}
+
+namespace {
+
 template <int MODE, int BC>
 void pair_launch(const GridDims &g, const float *kappa, const float *S, const unsigned char *tpl, const int *order,
                  const float *faces, const float *bnd, float *I_out, float *M_out, float *E_out, float *f_out,
-                 void *emax_bits, long long spin, int *status, const int *block_list, int nlist, cudaStream_t st) {
+                 void *emax_bits, long long spin, int *status, const int *block_list, int nlist, cudaStream_t st,
+                 const TailSplit *split) {
   const int parts = BC * BC * BC / 2 / pair_threads(BC);
   const int nblk = block_list ? nlist : g.nbx * g.nby * g.nbz;
   int dt, nstage;
   pair_staging(BC, g.dir_tile, dt, nstage);
+  // the tail split: whole grids only; the moment passes need its scratch
+  TailPlan tp;
+  tp.nfull = nblk * parts;
+  if (split && !block_list) {
+    const TailPlan q = plan_tail_split(BC, nblk, split->nsm, (g.ndir + dt - 1) / dt);
+    const bool room = MODE == 1 || (split->part && split->count && q.part_bytes <= split->part_bytes &&
+                                    q.slots <= split->slots);
+    if (q.k > 1 && room) tp = q;
+  }
+  const int grid = tp.nfull + (nblk * parts - tp.nfull) * tp.k;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // prologue overlaps the face pass's end
   attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.gridDim = dim3(nblk * parts);
+  cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(pair_threads(BC));
   cfg.dynamicSmemBytes = pair_smem_bytes(BC, nstage * dt);
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, cell_pair_kernel<MODE, BC>, g, parts, dt, nstage, kappa, S, tpl, order, faces, bnd, I_out,
-                     M_out, E_out, f_out, emax_bits, spin, status, block_list);
+                     M_out, E_out, f_out, emax_bits, spin, status, block_list, tp.nfull, tp.k,
+                     split ? split->part : nullptr, split ? split->count : nullptr);
 }
 
 template <typename R>
@@ -1626,7 +1725,7 @@ template <typename R>
 cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const R *S, const unsigned char *tpl,
                              const int *order, const R *faces, const R *bnd, R *I_out, R *M_out, R *E_out,
                              R *f_out, void *emax_bits, long long spin, int *status, cudaStream_t st,
-                             const int *block_list, int nlist) {
+                             const int *block_list, int nlist, const TailSplit *split) {
   if (block_list && nlist <= 0) return cudaSuccess;
   if constexpr (sizeof(R) == sizeof(float)) {
     if (g.paired && (g.B == 16 || g.B == 8)) {
@@ -1636,7 +1735,8 @@ cudaError_t launch_cell_pass(const GridDims &g, int mode, const R *kappa, const 
       float *Eo = reinterpret_cast<float *>(E_out), *fo = reinterpret_cast<float *>(f_out);
       const int mode2 = mode == 0 ? (M_out ? 0 : 2) : 1;
 #define VET_PAIR(MODE, BC) \
-  pair_launch<MODE, BC>(g, k, s, tpl, order, fc, bd, Io, Mo, Eo, fo, emax_bits, spin, status, block_list, nlist, st)
+  pair_launch<MODE, BC>(g, k, s, tpl, order, fc, bd, Io, Mo, Eo, fo, emax_bits, spin, status, block_list, nlist, st, \
+                        split)
       if (g.B == 16) {
         if (mode2 == 0) VET_PAIR(0, 16);
         else if (mode2 == 2) VET_PAIR(2, 16);
@@ -1745,7 +1845,8 @@ cudaError_t prepare_kernels() {
                                             cudaStream_t);                                                   \
   template cudaError_t launch_cell_pass<R>(const GridDims &, int, const R *, const R *, const unsigned char *, \
                                            const int *, const R *, const R *, R *, R *, R *, R *, void *,    \
-                                           long long, int *, cudaStream_t, const int *, int);                \
+                                           long long, int *, cudaStream_t, const int *, int,                 \
+                                           const TailSplit *);                                               \
   template cudaError_t launch_floor_fix_blocks<R>(const GridDims &, const int *, int, const R *, const void *, \
                                                   double, R *, cudaStream_t);                                \
   template cudaError_t launch_fill_boundary<R>(const GridDims &, const unsigned char *, const R *, R *,      \

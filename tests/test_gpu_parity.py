@@ -106,7 +106,7 @@ NEAR_PLANE_Q = np.array([np.sqrt(0.5), 1 / np.sqrt(10.0), 1 / np.sqrt(3.0), 0.2]
 
 @pytest.mark.parametrize("case", ["blob32", "lognormal48", "cloud", "ragged", "tiny_blocks", "unrotated8",
                                   "unrotated16", "near_plane8", "near_plane16", "single_block16", "vacuum",
-                                  "opaque", "block12"])
+                                  "opaque", "block12", "tail_split"])
 def test_fp32_closure_matches_oracle(ora, case):
     """The unrotated cases hold directions with an exactly zero component (the
     HEALPix equator ring, n_z = 0), where a direction and its antipode both
@@ -142,6 +142,9 @@ def test_fp32_closure_matches_oracle(ora, case):
         p = synth.lognormal_problem(n=32, B=8, nside=2, seed=29)
         p["kappa"] = np.full_like(p["kappa"], 1e4 / p["h"])
         Ib = np.random.default_rng(29).uniform(0, 0.5, (6, 48))
+    elif case == "tail_split":  # 256 paired cell-pass CTAs: the last partial wave runs as direction shares
+        p = synth.lognormal_problem(shape=(64, 64, 128), B=16, nside=4, seed=31)
+        Ib = np.random.default_rng(31).uniform(0, 0.5, (6, 192))
     elif case == "block12":  # a block edge the mirrored kernels do not take (generic passes)
         p = synth.lognormal_problem(shape=(24, 36, 48), B=12, nside=2, seed=30)
     elif case == "ragged":
