@@ -1,5 +1,6 @@
 """Batched closures of independent ragged grids (one CUDA graph, one branch
-per grid): identical to the grids' own closures, repeatable on graph replay,
+per grid): equal to the grids' own closures (bit for bit where those do not
+split their cell pass's last wave), repeatable on graph replay,
 within tolerance of the FP64 oracle, and unchanged (to rounding) by the
 autotuner's choice of tiles."""
 import numpy as np
@@ -75,8 +76,10 @@ def test_autotune_keeps_results_and_picks_valid_tiles():
 def test_config4_batch_of_64_ragged_grids(ora):
     """The 64-grid batch (edges 32..96, 8^3 or 16^3 blocks, 48 or 192
     directions): every grid against the FP64 oracle on every cell (2.4e9
-    cell-angles, about 40 s on 16 host cores), and four grids equal to their
-    own closures."""
+    cell-angles, about 40 s on 16 host cores), and four grids against their
+    own closures (to rounding: a lone grid of more than one wave of cell-pass
+    CTAs splits its last wave's work by directions, a batch member does not,
+    so the sums are added in another order)."""
     problems = synth.batched_problems(n_grids=64, seed0=100)
     specs, k, s = _batch(problems)
     batch = vet.Batch(specs)
@@ -89,7 +92,7 @@ def test_config4_batch_of_64_ragged_grids(ora):
         fr = torch.empty_like(f[i])
         ctx.closure(k[i], s[i], None, fr)
         ctx.sync()
-        assert torch.equal(fr, f[i])
+        assert (fr - f[i]).abs().max().item() < 1e-6, i
     worst = (0.0, 0.0, 0.0)
     for i, p in enumerate(problems):
         kk = p["kappa"].astype(np.float32).astype(np.float64)
