@@ -127,8 +127,33 @@ vet_status build_schedule(vet_ctx *c, int group) {
   }
   const long long nitems =
       vet::geom::build_schedule(nb, c->ob, group, nullptr, 1LL << 40, off.data(), lg.data(), paired);
-  std::vector<FaceItem> items((size_t)std::max<long long>(1, nitems));
-  vet::geom::build_schedule(nb, c->ob, group, items.data(), nitems, off.data(), lg.data(), paired);
+  std::vector<FaceItem> built((size_t)std::max<long long>(1, nitems));
+  vet::geom::build_schedule(nb, c->ob, group, built.data(), nitems, off.data(), lg.data(), paired);
+  // A level of at least one wave whose last partial wave is at most half a
+  // wave ends with its last r items cut in two (halves of their direction
+  // runs): the 2r shorter CTAs then finish in one round, sooner than the r
+  // whole ones.
+  std::vector<FaceItem> items;
+  items.reserve(built.size() + slots);
+  std::vector<int> noff(c->nlevels + 1, 0);
+  for (int L = 0; L < c->nlevels; ++L) {
+    noff[L] = (int)items.size();
+    const int n = off[L + 1] - off[L], r = (int)(n % slots);
+    const bool cut = n >= slots && r > 0 && 2LL * r <= slots && lg[L] >= 2;
+    for (int i = off[L]; i < off[L + 1]; ++i) {
+      const FaceItem it = built[i];
+      if (cut && i >= off[L + 1] - r && it.dir_count >= 2) {
+        const int h = it.dir_count / 2;
+        items.push_back({it.block, it.dir_begin, h, it.mirror_begin, it.octant});
+        items.push_back({it.block, it.dir_begin + h, it.dir_count - h, paired ? it.mirror_begin + h : 0, it.octant});
+      } else {
+        items.push_back(it);
+      }
+    }
+  }
+  noff[c->nlevels] = (int)items.size();
+  if (items.empty()) items.push_back(FaceItem{});
+  off = noff;
   FaceItem *d = nullptr;
   cudaError_t e = cudaMalloc((void **)&d, sizeof(FaceItem) * items.size());
   if (e) return cuda_err(c, e, "cudaMalloc(schedule)");
