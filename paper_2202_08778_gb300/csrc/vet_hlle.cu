@@ -35,23 +35,26 @@ __device__ __forceinline__ float cell_tau(float faa, float kap, float tenh) {
   return faa > 0.f ? __fdividef(0.5f * a * a, faa) : __int_as_float(0x7f800000);
 }
 
-// The correction sqrt((1 - e^-tau) / tau): 1 at tau = 0, 0 at tau = inf.
-// Below tau = 1/4 the ratio is log2(e) q(y), y = -tau log2(e), with q the
-// thin-segment cubic of the ray march (relative error 3.4e-7: no
+// The square of the correction, (1 - e^-tau) / tau: 1 at tau = 0, 0 at
+// tau = inf.  Below tau = 1/4 the ratio is log2(e) q(y), y = -tau log2(e),
+// with q the thin-segment cubic of the ray march (relative error 3.4e-7: no
 // cancellation); above, (1 - e^-tau) / tau with the MUFU exponential and a
-// fast quotient (a few ulp).
-__device__ __forceinline__ float correction(float tau) {
+// fast quotient (a few ulp; 1 / inf = 0 at tau = inf).
+__device__ __forceinline__ float correction_sq(float tau) {
   const float y = -1.4426950408889634f * tau;
   float e;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
   const float q = fmaf(fmaf(fmaf(vet::kThinQ3, y, vet::kThinQ2), y, vet::kThinQ1), y, vet::kThinQ0);
-  const float r = y > vet::kThinY ? 1.4426950408889634f * q : __fdividef(1.f - e, tau);
-  return tau < __int_as_float(0x7f800000) ? sqrtf(r) : 0.f;
+  return y > vet::kThinY ? 1.4426950408889634f * q : __fdividef(1.f - e, tau);
 }
 
+// sqrt(max(f_L, f_R)) c sqrt(corr) as one square root of the product, by
+// the MUFU square root (relative error of order 2^-23)
 __device__ __forceinline__ float face_speed(float fL, float tL, float fR, float tR, float c) {
-  const float s = sqrtf(fmaxf(fmaxf(fL, fR), 0.f));
-  return s == 0.f ? 0.f : s * c * correction(0.5f * (tL + tR));
+  const float x = fmaxf(fmaxf(fL, fR), 0.f) * correction_sq(0.5f * (tL + tR));
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return c * r;
 }
 
 // n / d for n < 2^31 and a divisor d >= 2 fixed per launch: m = ceil(2^32

@@ -767,7 +767,8 @@ VET_API vet_status vet_set_tuning(vet_ctx *ctx, int face_group, int dir_tile) {
     if (st != VET_OK) return st;
   }
   if (dir_tile > 0) {
-    const int dt = vet::cell_tile_fit(ctx->grid.block, dir_tile, ctx->fp64);
+    const int dt = ctx->dims.paired ? vet::pair_tile_fit(ctx->grid.block, dir_tile)
+                                    : vet::cell_tile_fit(ctx->grid.block, dir_tile, ctx->fp64);
     if (dt != ctx->dims.dir_tile) ++ctx->tuning_gen;
     ctx->dims.dir_tile = dt;
   }
@@ -777,7 +778,11 @@ VET_API vet_status vet_set_tuning(vet_ctx *ctx, int face_group, int dir_tile) {
 VET_API vet_status vet_get_tuning(const vet_ctx *ctx, int *face_group, int *dir_tile) {
   if (!ctx || !face_group || !dir_tile) return VET_EINVAL;
   *face_group = ctx->face_group;
-  *dir_tile = vet::cell_tile_fit(ctx->grid.block, ctx->dims.dir_tile > 0 ? ctx->dims.dir_tile : 4, ctx->fp64);
+  // the tile the cell pass actually runs with (the paired pass has its own
+  // default and ring fitting)
+  *dir_tile = ctx->dims.paired ? vet::pair_tile_fit(ctx->grid.block, ctx->dims.dir_tile)
+                               : vet::cell_tile_fit(ctx->grid.block, ctx->dims.dir_tile > 0 ? ctx->dims.dir_tile : 4,
+                                                    ctx->fp64);
   return VET_OK;
 }
 

@@ -234,6 +234,10 @@ size_t pass_smem_bytes(int B, int dirs, bool fp64);
 // Largest cell-pass direction tile (<= want) whose two buffers fit.
 int cell_tile_fit(int B, int want, bool fp64);
 
+// The direction tile the paired FP32 cell pass runs with for a requested
+// tile (0: untuned), after its staging ring is fitted to shared memory.
+int pair_tile_fit(int B, int want);
+
 // Dynamic shared memory of an unpaired cell-pass CTA with `nslots` staged
 // directions.
 size_t cell_smem_bytes(int B, int nslots, bool fp64);
