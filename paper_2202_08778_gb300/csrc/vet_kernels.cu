@@ -1239,30 +1239,63 @@ __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
     if (threadIdx.x == 0) split_count[slot] = 0;  // ready for the next call
   }
   if (MODE != 1) {
+    // Outputs: staged in the (now idle) staging ring as [value][z slot][y][x]
+    // over the CTA's 2L layers, then written row by row, so that every
+    // warp writes runs of B consecutive cells of a component (a host-mapped
+    // output then crosses the host link in whole runs, not 16-byte pieces)
+    constexpr int L = NT / B2, CELLS = 2 * NT, NV = kWantF ? 16 : 7, NM = kWantF ? 10 : 1;
+    const bool staged = (size_t)nstage * stage_bytes >= sizeof(float) * NV * CELLS;
     float emax = 0.f;
-    if (ok) {
+    if (__syncthreads_and(ok)) {  // also: every warp is done with the ring
       float Ms[2][10];
 #pragma unroll
       for (int m = 0; m < 10; ++m) {
         Ms[0][m] = mom[m].x;
         Ms[1][m] = mom[m].y;
       }
+      float *st = reinterpret_cast<float *>(ring);
+      const int zs = 2 * (qb / (B2 / 16) - part * (L / 2)) + (ln >> 4);  // the lower cell's z slot
+      const int li[2] = {(zs * B + cy) * B + cx, ((L + zs) * B + my) * B + mx};
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const long long gc = r ? gc2 : gc1;
         const float E = Ms[r][0];
+        float v[NV];
         if (kWantF) {
-          for (int m = 0; m < 10; ++m) M_out[m * g.ncell + gc] = Ms[r][m];
+#pragma unroll
+          for (int m = 0; m < 10; ++m) v[m] = Ms[r][m];
         } else {
-          E_out[gc] = E;
+          v[0] = E;
         }
-        if (E > 0.f) {
-          // correctly rounded, as in cell_pass_kernel
-          for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = Ms[r][4 + m] / E;
+#pragma unroll
+        for (int m = 0; m < 6; ++m)  // correctly rounded, as in cell_pass_kernel
+          v[NM + m] = E > 0.f ? Ms[r][4 + m] / E : (m < 3 ? 1.f / 3.f : 0.f);
+        if (staged) {
+#pragma unroll
+          for (int m = 0; m < NV; ++m) st[m * CELLS + li[r]] = v[m];
         } else {
-          for (int m = 0; m < 6; ++m) f_out[m * g.ncell + gc] = m < 3 ? 1.f / 3.f : 0.f;
+#pragma unroll
+          for (int m = 0; m < NV; ++m) {
+            float *dst = m < NM ? (kWantF ? M_out + m * g.ncell : E_out) : f_out + (m - NM) * g.ncell;
+            dst[gc] = v[m];
+          }
         }
         emax = fmaxf(emax, E);
+      }
+      if (staged) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < CELLS; i += NT) {
+          const int zsl = i / B2, y = (i / B) % B, x = i % B, zl = zsl < L ? zsl : zsl - L;
+          int lp = part * (L / 2) + (zl >> 1);
+          if (B == 16 && parts == 2) lp = (0x2130 >> (4 * lp)) & 15;
+          const int z = zsl < L ? 2 * lp + (zl & 1) : B - 1 - (2 * lp + (zl & 1));
+          const long long gi = ((long long)(bz * B + z) * g.ny + (by * B + y)) * g.nx + (bx * B + x);
+#pragma unroll
+          for (int m = 0; m < NV; ++m) {
+            float *dst = m < NM ? (kWantF ? M_out + m * g.ncell : E_out) : f_out + (m - NM) * g.ncell;
+            dst[gi] = st[m * CELLS + i];
+          }
+        }
       }
     }
     for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
