@@ -1406,6 +1406,7 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     }
   }
   const int total = cnt * nlive * NN;
+  const uint32_t slots_s = smem_u32(slots);
   for (int w0 = (int)threadIdx.x & ~31; w0 < total; w0 += blockDim.x) {
     const int wr = w0 + ((int)threadIdx.x & 31);
     const bool act = wr < total;
@@ -1413,23 +1414,32 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     const int q = w / NN, r = w - q * NN;
     const int j = nlive == 1 ? q : (nlive == 2 ? q >> 1 : (q * 21846) >> 16);
     const int ai = q - j * nlive;
-    const Tpl<float> T(slots + sb * j, TL);
-    const float *fin1 = reinterpret_cast<const float *>(slots + sb * j + TL.node_bytes);
-    const float *fin2 = reinterpret_cast<const float *>(slots + sb * cnt + fb3 * j);
+    // 32-bit shared addresses of the slot's template parts and both rays'
+    // incoming faces
+    const uint32_t ps = slots_s + (uint32_t)(sb * j);
+    const uint32_t f1 = ps + (uint32_t)TL.node_bytes, f2 = slots_s + (uint32_t)(sb * cnt + fb3 * j);
     const int a = (live >> (2 * ai)) & 3;
     const int ub = r / N1, uc = r - ub * N1;
     const int L0 = a == 0 ? B : ub;
     const int L1 = a == 1 ? B : (a == 0 ? ub : uc);
     const int L2 = a == 2 ? B : uc;
-    const int p0 = T.npos[L0], p1 = T.npos[N1 + L1], p2 = T.npos[2 * N1 + L2];
+    const uint32_t pp = ps + (uint32_t)TL.npos;
+    const int p0 = lds_s16(pp + 2 * L0), p1 = lds_s16(pp + 2 * (N1 + L1)), p2 = lds_s16(pp + 2 * (2 * N1 + L2));
     int last = p0, ae = 0, la = L0, lb = L1, lc = L2;
     if (p1 < last) { last = p1; ae = 1; la = L1; lb = L0; }
     if (p2 < last) { last = p2; ae = 2; la = L2; lb = L0; lc = L1; }
     const int row = (ae * 2) * N1 + la;
-    const int kb = T.nk[row], kc = T.nk[row + N1];
-    const float2 wb = T.nw[row], wc = T.nw[row + N1];
-    float2 I = make_float2(face_value<float>(fin1, g.fstride, B, ae, lb, lc, kb, kc, wb, wc),
-                           face_value<float>(fin2, g.fstride, B, ae, lb, lc, kb, kc, wb, wc));
+    const int kb = lds_s16(ps + TL.nk + 2 * row), kc = lds_s16(ps + TL.nk + 2 * (row + N1));
+    const uint2 wbu = lds_2x32(ps + TL.nw + 8 * row), wcu = lds_2x32(ps + TL.nw + 8 * (row + N1));
+    const float wbx = __uint_as_float(wbu.x), wby = __uint_as_float(wbu.y);
+    const float wcx = __uint_as_float(wcu.x), wcy = __uint_as_float(wcu.y);
+    const int ib = max(lb + kb, 0), ic = max(lc + kc, 0);
+    const uint32_t fo = 4u * (uint32_t)(ae * g.fstride + ib * W + ic);
+    const uint32_t a1 = f1 + fo, a2 = f2 + fo;
+    float2 I = make_float2(wby * (wcy * lds_f32(a1) + wcx * lds_f32(a1 + 4)) +
+                               wbx * (wcy * lds_f32(a1 + 4 * W) + wcx * lds_f32(a1 + 4 * W + 4)),
+                           wby * (wcy * lds_f32(a2) + wcx * lds_f32(a2 + 4)) +
+                               wbx * (wcy * lds_f32(a2 + 4 * W) + wcx * lds_f32(a2 + 4 * W + 4)));
     if (!act) last = -1;
     // lockstep aligned at the downwind end, as in the unpaired face pass; a
     // lane whose own ray is shorter steps on zeros without a load (a
@@ -1437,11 +1447,12 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     // four at a time in 16-byte pairs
     const int wl = __reduce_max_sync(0xffffffffu, last);
     if (wl >= 0) {
-      const int c0 = T.h->sgn[0] > 0 ? L0 - 1 : B - L0;
-      const int c1 = T.h->sgn[1] > 0 ? L1 - 1 : B - L1;
-      const int c2 = T.h->sgn[2] > 0 ? L2 - 1 : B - L2;
+      const uint4 hd = lds_4x32(ps + 16);  // (sgn0, sgn1, sgn2, ext)
+      const int c0 = (int)hd.x > 0 ? L0 - 1 : B - L0;
+      const int c1 = (int)hd.y > 0 ? L1 - 1 : B - L1;
+      const int c2 = (int)hd.z > 0 ? L2 - 1 : B - L2;
       const uint32_t tb = last >= 0 ? tile_s + 16u * (uint32_t)(c0 + ts.sy * c1 + ts.sz * c2) : id_s;
-      const uint32_t ev = smem_u32(T.nev);
+      const uint32_t ev = ps + (uint32_t)TL.nev;
       int e = wl;
       if (!(e & 1)) {  // to an odd index: event pairs (e - 1, e) are 16-byte aligned
         const float2 v = lds_f2(ev + 8 * e);
