@@ -59,7 +59,7 @@ typedef enum {
   VET_ENOMEM = 2,       /* device or host allocation failed */
   VET_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
   VET_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
-  VET_EUNSUPPORTED = 5  /* valid request this build cannot serve */
+  VET_EUNSUPPORTED = 5  /* valid request the library cannot serve */
 } vet_status;
 
 #define VET_FP32 0 /* float fields, FP32 ray march and moments */
@@ -213,7 +213,7 @@ const char *vet_batch_last_error(const vet_batch *batch);
  * Learned closure (not in the paper, whose closures are the exact VET, M1
  * and Eddington, Sec. 2.2.5 and App. A): a small 3D convolutional network
  * predicts f from local features; the exact ray tracer above is its fallback
- * and the judge of its error.
+ * and the reference for its error.
  *
  * Features per cell (6): 1 (validity; the zero padding at the domain edge
  * reads 0), log10(kappa h), log10 S and log10 E each minus its mean over the
@@ -241,7 +241,7 @@ const char *vet_batch_last_error(const vet_batch *batch);
 typedef struct vet_model vet_model;
 
 /* Create a model on `device` with `channels` hidden channels (32 is the
- * only value this build supports).  Weights start at zero: call
+ * only value the library supports).  Weights start at zero: call
  * vet_model_set_params. */
 vet_status vet_model_create(vet_model **out, int channels, int device);
 vet_status vet_model_destroy(vet_model *model);
