@@ -850,6 +850,14 @@ struct vet_batch {
   cudaEvent_t forked = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<const void *> key;      // pointers the graph was captured with
+  // merged cell passes: the grids' descriptors and (grid, block) work items
+  // in device memory, grouped by block edge (16 first), each group's grids
+  // largest first
+  vet::CellGrid *d_grids = nullptr;
+  int2 *d_items = nullptr;
+  size_t items_cap = 0;
+  std::vector<cudaEvent_t> group_done;  // one per (block edge, direction tile) group
+  bool merged = true;  // one cell-pass launch per block edge (else one per grid)
   std::string err;
 };
 
@@ -867,10 +875,149 @@ void free_batch(vet_batch *b) {
   for (auto e : b->joined) cudaEventDestroy(e);
   if (b->origin) cudaStreamDestroy(b->origin);
   if (b->forked) cudaEventDestroy(b->forked);
+  for (auto e : b->group_done)
+    if (e) cudaEventDestroy(e);
+  b->group_done.clear();
+  cudaFree(b->d_grids);
+  cudaFree(b->d_items);
   for (auto c : b->ctx) free_ctx(c);
   delete b;
 }
 
+
+// Whether a batch's cell passes can run merged: FP32 grids whose paired
+// cell pass runs (block edges 8 and 16), M wanted by all grids or by none.
+bool can_merge(const vet_batch *b, float *const *M_out) {
+  if (!b->merged) return false;
+  int with_M = 0;
+  for (int i = 0; i < b->n; ++i) {
+    const vet_ctx *c = b->ctx[i];
+    if (c->fp64 || !c->dims.paired || (c->grid.block != 8 && c->grid.block != 16)) return false;
+    with_M += (M_out && M_out[i]) ? 1 : 0;
+  }
+  return with_M == 0 || with_M == b->n;
+}
+
+// One merged cell-pass launch: the grids of one block edge and one
+// direction tile (so that each grid computes exactly what its own closure
+// at its tuning computes).
+struct MergedGroup {
+  int B, dt, first, nitems, lead;  // lead: the grid on whose branch the launch goes
+  std::vector<int> members;
+};
+
+// Descriptors and work items of the merged cell passes, uploaded before
+// capture: groups of one block edge and direction tile, edge 16 first; each
+// group's grids with more blocks first (the long ones start first, the
+// small ones fill in).
+vet_status upload_merged(vet_batch *b, const float *const *kappa, const float *const *S, float *const *f_out,
+                         float *const *M_out, std::vector<MergedGroup> &groups) {
+  std::vector<vet::CellGrid> grids(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    vet_ctx *c = b->ctx[i];
+    vet::CellGrid &g = grids[i];
+    g.g = c->dims;
+    g.kappa = kappa[i];
+    g.S = S[i];
+    g.tpl = (const unsigned char *)c->d_tpl;
+    g.order = c->d_cell_order;
+    g.faces = (const float *)c->d_faces;
+    g.bnd = (const float *)c->d_bnd;
+    g.M_out = M_out ? M_out[i] : nullptr;
+    g.E_out = (float *)c->d_E;
+    g.f_out = f_out[i];
+    g.emax_bits = c->d_emax;
+    g.status = c->d_status;
+  }
+  groups.clear();
+  for (int B : {16, 8})
+    for (int i = 0; i < b->n; ++i) {
+      const vet_ctx *c = b->ctx[i];
+      if (c->grid.block != B) continue;
+      const int dt = vet::pair_tile_fit(B, c->dims.dir_tile);
+      auto it = std::find_if(groups.begin(), groups.end(), [&](const MergedGroup &m) { return m.B == B && m.dt == dt; });
+      if (it == groups.end()) {
+        groups.push_back(MergedGroup{B, dt, 0, 0, i, {}});
+        it = groups.end() - 1;
+      }
+      it->members.push_back(i);
+    }
+  std::vector<int2> items;
+  for (auto &m : groups) {
+    std::stable_sort(m.members.begin(), m.members.end(),
+                     [&](int x, int y) { return b->ctx[x]->nblk > b->ctx[y]->nblk; });
+    m.lead = m.members[0];
+    m.first = (int)items.size();
+    for (int i : m.members)
+      for (int blk = 0; blk < b->ctx[i]->nblk; ++blk) items.push_back(make_int2(i, blk));
+    m.nitems = (int)items.size() - m.first;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!b->d_grids && (e = cudaMalloc((void **)&b->d_grids, sizeof(vet::CellGrid) * b->n)))
+    return batch_err(b, VET_ENOMEM, std::string("cudaMalloc(batch grids): ") + cudaGetErrorString(e));
+  if (items.size() > b->items_cap) {
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    b->items_cap = 0;
+    if ((e = cudaMalloc((void **)&b->d_items, sizeof(int2) * items.size())))
+      return batch_err(b, VET_ENOMEM, std::string("cudaMalloc(batch items): ") + cudaGetErrorString(e));
+    b->items_cap = items.size();
+  }
+  if ((e = cudaMemcpy(b->d_grids, grids.data(), sizeof(vet::CellGrid) * b->n, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice)))
+    return batch_err(b, VET_ECUDA, std::string("upload batch items: ") + cudaGetErrorString(e));
+  while (b->group_done.size() < groups.size()) {
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)))
+      return batch_err(b, VET_ECUDA, std::string("event: ") + cudaGetErrorString(e));
+    b->group_done.push_back(ev);
+  }
+  return VET_OK;
+}
+
+// The captured work of a merged batch: each grid's face pass on its own
+// branch; per group, once its grids' face passes are done, one cell pass
+// over all their blocks on the lead grid's branch; then each grid's floor
+// rule on its branch.
+vet_status capture_merged(vet_batch *b, const float *const *kappa, const float *const *S, const float *const *Ib,
+                          float *const *f_out, float *const *M_out, const std::vector<MergedGroup> &groups,
+                          cudaError_t &e) {
+  const bool with_M = M_out && M_out[0];
+  for (int i = 0; i < b->n && !e; ++i) {
+    vet_ctx *c = b->ctx[i];
+    if ((e = cudaStreamWaitEvent(b->branch[i], b->forked, 0))) break;
+    if ((e = cudaMemsetAsync(c->d_emax, 0, 8, b->branch[i]))) break;
+    vet_status st = run_face_pass<float>(c, kappa[i], S[i], Ib ? Ib[i] : nullptr, b->branch[i]);
+    if (st != VET_OK) {
+      b->err = "grid " + std::to_string(i) + ": " + c->err;
+      return st;
+    }
+    e = cudaEventRecord(b->joined[i], b->branch[i]);
+  }
+  std::vector<int> group_of(b->n, -1);
+  for (size_t k = 0; k < groups.size() && !e; ++k) {
+    const MergedGroup &m = groups[k];
+    cudaStream_t gs = b->branch[m.lead];
+    for (int i : m.members) {
+      group_of[i] = (int)k;
+      if (!e && i != m.lead) e = cudaStreamWaitEvent(gs, b->joined[i], 0);
+    }
+    if (!e)
+      e = vet::launch_cell_pass_merged(m.B, with_M, m.dt, b->d_grids, b->d_items + m.first, m.nitems,
+                                       b->ctx[m.lead]->spin, gs);
+    if (!e) e = cudaEventRecord(b->group_done[k], gs);
+  }
+  for (int i = 0; i < b->n && !e; ++i) {
+    vet_ctx *c = b->ctx[i];
+    const MergedGroup &m = groups[group_of[i]];
+    if (i != m.lead && (e = cudaStreamWaitEvent(b->branch[i], b->group_done[group_of[i]], 0))) break;
+    const float *E = with_M ? M_out[i] : (const float *)c->d_E;
+    if ((e = vet::launch_floor_fix<float>(c->dims.ncell, E, 1, c->d_emax, 1e-30, f_out[i], b->branch[i]))) break;
+    if ((e = cudaEventRecord(b->joined[i], b->branch[i]))) break;
+    e = cudaStreamWaitEvent(b->origin, b->joined[i], 0);
+  }
+  return VET_OK;
+}
 }  // namespace
 
 VET_API vet_status vet_batch_create(vet_batch **out, int n, const vet_grid *grids, const vet_config *cfgs) {
@@ -943,17 +1090,26 @@ VET_API vet_status vet_batch_closure(vet_batch *b, const float *const *kappa, co
   }
   DeviceGuard dg(b->device);
   if (!b->exec || key != b->key) {
-    // capture one closure per grid, each on its own branch of the graph
+    // capture one closure per grid, each on its own branch of the graph (the
+    // cell passes of grids of one block edge merged into one launch where
+    // they can be)
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
+    }
+    const bool merged = can_merge(b, M_out);
+    std::vector<MergedGroup> groups;
+    if (merged) {
+      vet_status su = upload_merged(b, kappa, S, f_out, M_out, groups);
+      if (su != VET_OK) return su;
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
     if (e) return batch_err(b, VET_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
     vet_status st = VET_OK;
     e = cudaEventRecord(b->forked, b->origin);
-    for (int i = 0; i < b->n && !e && st == VET_OK; ++i) {
+    if (merged && !e) st = capture_merged(b, kappa, S, Ib, f_out, M_out, groups, e);
+    for (int i = 0; !merged && i < b->n && !e && st == VET_OK; ++i) {
       if ((e = cudaStreamWaitEvent(b->branch[i], b->forked, 0))) break;
       vet_ctx *c = b->ctx[i];
       const bool timing = c->timing;

@@ -187,6 +187,27 @@ struct TailPlan {
 };
 TailPlan plan_tail_split(int B, int nblk, int nsm, int ntiles);
 
+// One grid of a merged launch of the paired FP32 cell pass (the batched
+// closure): what a single grid's launch passes as arguments.  M_out null:
+// E goes to E_out (the floor rule's input) and only f is written.
+struct CellGrid {
+  GridDims g;
+  const float *kappa, *S;
+  const unsigned char *tpl;
+  const int *order;
+  const float *faces, *bnd;
+  float *M_out, *E_out, *f_out;
+  void *emax_bits;
+  int *status;
+};
+
+// The paired FP32 cell pass (moments and f) over the blocks of several grids
+// of block edge B (8 or 16) in one launch: items[i] = (grid index, block
+// index), both device arrays; with_M: every grid writes M (else none does);
+// one direction tile for all (0: untuned).
+cudaError_t launch_cell_pass_merged(int B, bool with_M, int dir_tile, const CellGrid *grids, const int2 *items,
+                                   int nitems, long long spin, cudaStream_t st);
+
 // What the caller provides for the split: the SM count and the scratch
 // (part: part_bytes, count: slots zeroed ints).  part == nullptr: no split
 // of the moment passes (the trace needs no scratch).

@@ -958,20 +958,37 @@ static_assert(offsetof(TplHead<float>, sgn) == 16 && offsetof(TplHead<float>, ex
                   offsetof(TplHead<float>, mirror) == 32 && offsetof(TplHead<float>, cp) % 16 == 0,
               "TplHead<float> layout");
 
-template <int MODE, int BC>
+template <int MODE, int BC, bool MERGED>
 __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
-    cell_pair_kernel(GridDims g, int parts, int dt, int nstage, const float *__restrict__ kappa,
-                     const float *__restrict__ S, const unsigned char *__restrict__ tpl_g,
-                     const int *__restrict__ order, const float *__restrict__ faces, const float *__restrict__ bnd,
-                     float *__restrict__ I_out, float *__restrict__ M_out, float *__restrict__ E_out,
-                     float *__restrict__ f_out, void *emax_bits, long long spin_limit, int *status,
-                     const int *__restrict__ block_list, int nfull, int ksplit, float *__restrict__ split_part,
-                     int *__restrict__ split_count) {
+    cell_pair_kernel(GridDims g_arg, int parts, int dt, int nstage, const float *__restrict__ kappa_arg,
+                     const float *__restrict__ S_arg, const unsigned char *__restrict__ tpl_arg,
+                     const int *__restrict__ order_arg, const float *__restrict__ faces_arg,
+                     const float *__restrict__ bnd_arg, float *__restrict__ I_out, float *__restrict__ M_arg,
+                     float *__restrict__ E_arg, float *__restrict__ f_arg, void *emax_arg, long long spin_limit,
+                     int *status_arg, const int *__restrict__ block_list, int nfull, int ksplit,
+                     float *__restrict__ split_part, int *__restrict__ split_count,
+                     const CellGrid *__restrict__ grids, const int2 *__restrict__ items) {
   constexpr int B = BC, B2 = B * B, NT = pair_threads(BC);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kPairStagesMax], empty[kPairStagesMax];
   constexpr int kOrdMax = 1024;  // direction sets up to nside = 8 keep their order in shared memory
   __shared__ int s_ord[kOrdMax];
+  // a merged launch (several grids of one block edge) takes its grid from the
+  // work item's entry of `grids`; a single grid's launch from the arguments
+  const CellGrid *gd = nullptr;
+  if constexpr (MERGED) gd = grids + items[(int)blockIdx.x / parts].x;
+  const GridDims g = MERGED ? gd->g : g_arg;
+  const float *__restrict__ kappa = MERGED ? gd->kappa : kappa_arg;
+  const float *__restrict__ S = MERGED ? gd->S : S_arg;
+  const unsigned char *__restrict__ tpl_g = MERGED ? gd->tpl : tpl_arg;
+  const int *__restrict__ order = MERGED ? gd->order : order_arg;
+  const float *__restrict__ faces = MERGED ? gd->faces : faces_arg;
+  const float *__restrict__ bnd = MERGED ? gd->bnd : bnd_arg;
+  float *__restrict__ M_out = MERGED ? gd->M_out : M_arg;
+  float *__restrict__ E_out = MERGED ? gd->E_out : E_arg;
+  float *__restrict__ f_out = MERGED ? gd->f_out : f_arg;
+  void *emax_bits = MERGED ? gd->emax_bits : emax_arg;
+  int *status = MERGED ? gd->status : status_arg;
   const bool ord_smem = g.ndir <= kOrdMax;
   const TileShape ts = cell_tile(B);
   const TplLayout TL = tpl_layout<float>(B);
@@ -993,7 +1010,7 @@ __global__ void __launch_bounds__(pair_threads(BC), pair_min_ctas(BC))
     cta = nfull + slot;
   }
   const int item = cta / parts, part = parts - 1 - (cta - item * parts);
-  const int blk = block_list ? block_list[item] : item;
+  const int blk = MERGED ? items[item].y : (block_list ? block_list[item] : item);
   const int bx = blk % g.nbx, by = (blk / g.nbx) % g.nby, bz = blk / (g.nbx * g.nby);
   constexpr int nwarps = NT / 32;
   const int ntiles_all = (g.ndir + dt - 1) / dt, nshares = slot >= 0 ? ksplit : 1;
@@ -1735,9 +1752,31 @@ void pair_launch(const GridDims &g, const float *kappa, const float *S, const un
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, cell_pair_kernel<MODE, BC>, g, parts, dt, nstage, kappa, S, tpl, order, faces, bnd, I_out,
+  cudaLaunchKernelEx(&cfg, cell_pair_kernel<MODE, BC, false>, g, parts, dt, nstage, kappa, S, tpl, order, faces, bnd, I_out,
                      M_out, E_out, f_out, emax_bits, spin, status, block_list, tp.nfull, tp.k,
-                     split ? split->part : nullptr, split ? split->count : nullptr);
+                     split ? split->part : nullptr, split ? split->count : nullptr, nullptr, nullptr);
+}
+
+// One launch of the paired cell pass over the blocks of several grids of
+// block edge BC: items[i] = (grid, block), grids as the single-grid
+// launches' arguments.
+template <int MODE, int BC>
+void pair_launch_merged(int dir_tile, const CellGrid *grids, const int2 *items, int nitems, long long spin,
+                        cudaStream_t st) {
+  const int parts = BC * BC * BC / 2 / pair_threads(BC);
+  int dt, nstage;
+  pair_staging(BC, dir_tile, dt, nstage);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nitems * parts);
+  cfg.blockDim = dim3(pair_threads(BC));
+  cfg.dynamicSmemBytes = pair_smem_bytes(BC, nstage * dt);
+  cfg.stream = st;
+  const int total = nitems * parts;
+  cudaLaunchKernelEx(&cfg, cell_pair_kernel<MODE, BC, true>, GridDims{}, parts, dt, nstage, (const float *)nullptr,
+                     (const float *)nullptr, (const unsigned char *)nullptr, (const int *)nullptr,
+                     (const float *)nullptr, (const float *)nullptr, (float *)nullptr, (float *)nullptr,
+                     (float *)nullptr, (float *)nullptr, (void *)nullptr, spin, (int *)nullptr, (const int *)nullptr,
+                     total, 1, (float *)nullptr, (int *)nullptr, grids, items);
 }
 
 template <typename R>
@@ -1753,10 +1792,12 @@ cudaError_t set_smem_attrs() {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
   }
-  const void *pfns[] = {(const void *)cell_pair_kernel<0, 8>,  (const void *)cell_pair_kernel<0, 16>,
-                        (const void *)cell_pair_kernel<1, 8>,  (const void *)cell_pair_kernel<1, 16>,
-                        (const void *)cell_pair_kernel<2, 8>,  (const void *)cell_pair_kernel<2, 16>,
-                        (const void *)face_pair_kernel<8>,     (const void *)face_pair_kernel<16>};
+  const void *pfns[] = {(const void *)cell_pair_kernel<0, 8, false>,  (const void *)cell_pair_kernel<0, 16, false>,
+                        (const void *)cell_pair_kernel<1, 8, false>,  (const void *)cell_pair_kernel<1, 16, false>,
+                        (const void *)cell_pair_kernel<2, 8, false>,  (const void *)cell_pair_kernel<2, 16, false>,
+                        (const void *)cell_pair_kernel<0, 8, true>,   (const void *)cell_pair_kernel<0, 16, true>,
+                        (const void *)cell_pair_kernel<2, 8, true>,   (const void *)cell_pair_kernel<2, 16, true>,
+                        (const void *)face_pair_kernel<8>,            (const void *)face_pair_kernel<16>};
   for (const void *f : pfns) {  // less their static shared memory
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, f);
@@ -1777,6 +1818,21 @@ cudaError_t launch_face_level(const GridDims &g, const R *kappa, const R *S, con
   if (g.B == 16) face_launch<R, 16>(g, kappa, S, tpl, items, nitems, max_dirs, faces, bnd, spin, status, st);
   else if (g.B == 8) face_launch<R, 8>(g, kappa, S, tpl, items, nitems, max_dirs, faces, bnd, spin, status, st);
   else face_launch<R, 0>(g, kappa, S, tpl, items, nitems, max_dirs, faces, bnd, spin, status, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_pass_merged(int B, bool with_M, int dir_tile, const CellGrid *grids, const int2 *items,
+                                   int nitems, long long spin, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  if (B == 16) {
+    if (with_M) pair_launch_merged<0, 16>(dir_tile, grids, items, nitems, spin, st);
+    else pair_launch_merged<2, 16>(dir_tile, grids, items, nitems, spin, st);
+  } else if (B == 8) {
+    if (with_M) pair_launch_merged<0, 8>(dir_tile, grids, items, nitems, spin, st);
+    else pair_launch_merged<2, 8>(dir_tile, grids, items, nitems, spin, st);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
