@@ -3,11 +3,16 @@ FP64 oracle (oracle/hlle.py): every face of ragged grids along all three
 axes, including cells with no radiation along the axis (f_aa = 0) and
 transparent cells (kappa = 0), and on the tensor of a traced closure.
 
+Grids whose nx is a multiple of 4 run the kernel's 16-byte path, the others
+(and arrays that are not 16-byte aligned) its scalar path; both are checked.
+
 Tolerance: the FP32 path takes about ten roundings and approximations of a
-few ulp each (the product 10 h kappa, its square, a fast quotient by 2 f_aa,
-the face mean, the thin-segment cubic (3.4e-7) or the hardware exponential
-and a fast quotient, sqrtf and two products); the correction's sensitivity
-to tau is at most 1/2 in relative terms, so 2e-6 relative bounds it."""
+few ulp each (the per-launch constant (10 h)^2 log2(e) / 4, its products
+with kappa twice and with the hardware reciprocal of f_aa, the sum of the
+two cells' halves, the thin-segment cubic (3.4e-7) or the hardware
+exponential and reciprocal, the hardware square root and the product by c);
+the correction's sensitivity to tau is at most 1/2 in relative terms, so
+2e-6 relative bounds it."""
 import numpy as np
 import pytest
 
@@ -25,15 +30,23 @@ from paper_2202_08778_gb300 import vet  # noqa: E402
 RTOL = 2e-6
 
 
-def _check(f32, k32, h, c=1.0):
+def _offset(t, shift):
+    """t on the device, starting `shift` floats into a larger buffer (shift
+    1: 4 bytes past a 16-byte boundary)."""
+    buf = torch.empty(t.numel() + shift, device="cuda")
+    buf[shift:] = t.reshape(-1).cuda()
+    return buf[shift:]
+
+
+def _check(f32, k32, h, c=1.0, shift=0):
     nz, ny, nx = k32.shape
-    fd = torch.from_numpy(np.ascontiguousarray(f32.reshape(6, -1))).cuda()
-    kd = torch.from_numpy(np.ascontiguousarray(k32)).cuda()
+    fd = _offset(torch.from_numpy(np.ascontiguousarray(f32.reshape(-1))), shift)
+    kd = _offset(torch.from_numpy(np.ascontiguousarray(k32.reshape(-1))), shift)
     worst = 0.0
     for axis in range(3):
         ext = [nz, ny, nx]
         ext[2 - axis] += 1
-        C = torch.empty(int(np.prod(ext)), device="cuda")
+        C = _offset(torch.zeros(int(np.prod(ext))), shift)
         vet.hlle_wavespeed((nz, ny, nx), h, fd, kd, C, axis, c)
         torch.cuda.synchronize()
         got = C.cpu().numpy().reshape(ext)
@@ -45,21 +58,36 @@ def _check(f32, k32, h, c=1.0):
     return worst
 
 
+def _random_fields(rng, shape):
+    f = np.zeros((6,) + shape, dtype=np.float32)
+    f[:3] = rng.uniform(0.0, 1.0, (3,) + shape)
+    f[:3] /= f[:3].sum(0)
+    k = rng.lognormal(0.0, 2.5, shape).astype(np.float32)
+    # degenerate cells: no radiation along an axis, transparent cells
+    f[0].flat[:: 7] = 0.0
+    f[1].flat[3:: 11] = 0.0
+    k.flat[2:: 5] = 0.0
+    return f, k
+
+
 def test_random_tensors_on_ragged_grids():
     rng = np.random.default_rng(11)
-    for shape in ((5, 7, 9), (16, 3, 33), (1, 1, 4)):
-        nz, ny, nx = shape
-        f = np.zeros((6,) + shape, dtype=np.float32)
-        f[:3] = rng.uniform(0.0, 1.0, (3,) + shape)
-        f[:3] /= f[:3].sum(0)
-        k = rng.lognormal(0.0, 2.5, shape).astype(np.float32)
-        # degenerate cells: no radiation along an axis, transparent cells
-        f[0].flat[:: 7] = 0.0
-        f[1].flat[3:: 11] = 0.0
-        k.flat[2:: 5] = 0.0
+    # nx 9 and 33: scalar path; 4, 12 and 8: 16-byte path with ragged ny, nz
+    for shape in ((5, 7, 9), (16, 3, 33), (1, 1, 4), (3, 5, 12), (7, 1, 8)):
+        f, k = _random_fields(rng, shape)
         err = _check(f, k, 1.0 / max(shape))
         print(f"hlle {shape}: max rel err {err:.2e}")
         assert err < RTOL
+
+
+def test_unaligned_arrays_take_the_scalar_path():
+    """nx a multiple of 4 but the arrays 4 bytes off a 16-byte boundary: the
+    scalar path, with the same results as the aligned call."""
+    rng = np.random.default_rng(12)
+    f, k = _random_fields(rng, (4, 6, 16))
+    err = _check(f, k, 1.0 / 16, shift=1)
+    print(f"hlle unaligned: max rel err {err:.2e}")
+    assert err < RTOL
 
 
 def test_on_a_traced_closure():
