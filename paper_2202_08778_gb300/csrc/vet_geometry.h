@@ -393,6 +393,32 @@ inline bool mirrored_cell_pair(const unsigned char *ta, const unsigned char *tb,
 // (the order of mirror_octant_order).
 // Writes level_off[0..nlevels] and, when items != nullptr, the items.
 // Returns the number of items, or -1 if it exceeds `cap`.
+// Node order of the paired face pass for one template: for each face axis
+// a, the (B+1)^2 nodes (ub, uc) of a block's downwind face, as ub (B+1) + uc,
+// sorted by the index of their ray's exit event (ties by node index).  The
+// face pass hands consecutive entries to the lanes of a warp, which march in
+// lockstep for as many steps as their longest ray: in row order their rays
+// differ in length by up to a block edge's worth of events (0.59 of the
+// lane-steps useful on the 192-direction set), sorted they nearly agree.
+template <typename R>
+inline void node_order(const unsigned char *tpl, int B, uint16_t *out) {
+  const TplLayout L = tpl_layout<R>(B);
+  const int16_t *npos = reinterpret_cast<const int16_t *>(tpl + L.npos);
+  const int N1 = B + 1, NN = N1 * N1;
+  std::vector<int> last(NN);
+  for (int a = 0; a < 3; ++a) {
+    uint16_t *o = out + a * NN;
+    for (int r = 0; r < NN; ++r) {
+      const int ub = r / N1, uc = r % N1;
+      // upwind-frame node coordinates: B along the face's axis
+      const int L0 = a == 0 ? B : ub, L1 = a == 1 ? B : (a == 0 ? ub : uc), L2 = a == 2 ? B : uc;
+      last[r] = std::min({(int)npos[L0], (int)npos[N1 + L1], (int)npos[2 * N1 + L2]});
+      o[r] = (uint16_t)r;
+    }
+    std::stable_sort(o, o + NN, [&](uint16_t x, uint16_t y) { return last[x] < last[y]; });
+  }
+}
+
 inline long long build_schedule(const int nb[3], const int ob[9], int group, FaceItem *items, long long cap,
                                 int *level_off, const int *level_group = nullptr, bool paired = false) {
   const int nlevels = nb[0] + nb[1] + nb[2] - 2;

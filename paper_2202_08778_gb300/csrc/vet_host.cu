@@ -34,6 +34,7 @@ struct vet_ctx {
   void *d_tpl = nullptr;         // N template blobs, internal (octant-sorted) order
   FaceItem *d_items = nullptr;
   int *d_cell_order = nullptr;   // cell-pass visiting order of internal directions
+  uint16_t *d_node_order = nullptr;  // paired face pass: face nodes by ray length (dims.node_order)
   void *d_faces = nullptr;       // [N][blocks][3][fstride], upwind frame, padded
   void *d_emax = nullptr;        // 8 bytes: bit pattern of max E (nonnegative)
   void *d_E = nullptr;           // [cells] E when the caller does not want M
@@ -91,6 +92,7 @@ void free_ctx(vet_ctx *c) {
   cudaFree(c->d_tpl);
   cudaFree(c->d_items);
   cudaFree(c->d_cell_order);
+  cudaFree(c->d_node_order);
   cudaFree(c->d_faces);
   cudaFree(c->d_emax);
   cudaFree(c->d_E);
@@ -296,6 +298,17 @@ vet_status build_context(vet_ctx *c) {
   if ((e = cudaMalloc((void **)&c->d_cell_order, sizeof(int) * N))) return cuda_err(c, e, "cudaMalloc(order)");
   if ((e = cudaMemcpy(c->d_cell_order, cell_order.data(), sizeof(int) * N, cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload order");
+  if (c->dims.face_paired) {
+    const int NN = (B + 1) * (B + 1);
+    std::vector<uint16_t> nord((size_t)N * 3 * NN);
+    for (int i = 0; i < N; ++i)
+      vet::geom::node_order<R>(tpl.data() + (size_t)i * tbytes, B, nord.data() + (size_t)i * 3 * NN);
+    if ((e = cudaMalloc((void **)&c->d_node_order, sizeof(uint16_t) * nord.size())))
+      return cuda_err(c, e, "cudaMalloc(node order)");
+    if ((e = cudaMemcpy(c->d_node_order, nord.data(), sizeof(uint16_t) * nord.size(), cudaMemcpyHostToDevice)))
+      return cuda_err(c, e, "upload node order");
+    c->dims.node_order = c->d_node_order;
+  }
   if ((e = cudaMemcpy(c->d_coef, coef.data(), sizeof(R) * coef.size(), cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload coefficients");
   if ((e = vet::prepare_kernels())) return cuda_err(c, e, "cudaFuncSetAttribute");

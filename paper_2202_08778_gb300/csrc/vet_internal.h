@@ -119,6 +119,10 @@ struct GridDims {
   int dir_tile;       // directions per cell-pass tile (0: default)
   int paired;         // 1: the cell order lists antipodal pairs (d, -d), see the paired cell pass
   int face_paired;    // 1: face-pass items are mirrored block pairs, see the paired face pass
+  // paired face pass: per template (internal order) and face axis, the
+  // (B+1)^2 face nodes by ascending node-ray length, [N][3][(B+1)^2]
+  // (null: row order)
+  const uint16_t *node_order;
 };
 
 // Shared-memory kappa/S tiles of a block, in entries of 8 bytes (kappa, S) or,

@@ -1428,7 +1428,7 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     const int wr = w0 + ((int)threadIdx.x & 31);
     const bool act = wr < total;
     const int w = act ? wr : total - 1;
-    const int q = w / NN, r = w - q * NN;
+    const int q = w / NN, k = w - q * NN;
     const int j = nlive == 1 ? q : (nlive == 2 ? q >> 1 : (q * 21846) >> 16);
     const int ai = q - j * nlive;
     // 32-bit shared addresses of the slot's template parts and both rays'
@@ -1436,6 +1436,12 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     const uint32_t ps = slots_s + (uint32_t)(sb * j);
     const uint32_t f1 = ps + (uint32_t)TL.node_bytes, f2 = slots_s + (uint32_t)(sb * cnt + fb3 * j);
     const int a = (live >> (2 * ai)) & 3;
+    // the k-th node of the face by ray length, every other face of the item
+    // taken from its longest ray down, so that a warp that straddles two
+    // faces joins rays of similar length too
+    const int r = g.node_order ? (int)__ldg(g.node_order + ((size_t)(it.dir_begin + j) * 3 + a) * NN +
+                                            ((q & 1) ? NN - 1 - k : k))
+                               : k;
     const int ub = r / N1, uc = r - ub * N1;
     const int L0 = a == 0 ? B : ub;
     const int L1 = a == 1 ? B : (a == 0 ? ub : uc);
