@@ -6,6 +6,8 @@
 //  - the paired cell pass marches every antipodal pair of a rotated set as a
 //    mirrored pair, and never one with a zero direction component (whose
 //    sign the antipode keeps) of the unrotated set;
+//  - the paired face pass's node order is, per template and face axis, a
+//    permutation of the face's nodes by non-decreasing node-ray length;
 //  - the paired face-pass schedule, with each item's point-mirrored block and
 //    antipodal directions added, lists every (block, direction) of the
 //    unpaired schedule exactly once, level by level.
@@ -14,6 +16,7 @@
 // plane crossings of a direction tie); "unrotated" checks instead that the
 // HEALPix set itself, with its z = 0 ring, is refused by the face pass's
 // mirror order and its zero-component pairs by the cell pass's pairing.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -97,6 +100,33 @@ int main(int argc, char **argv) {
       if (other != j && vet::geom::mirror_node_templates<float>(T(i), T(other), B))
         return fail("a non-antipodal pair passed the node mirror check");
     }
+  // the paired face pass's node order: per template and face axis a
+  // permutation of the (B+1)^2 face nodes with the node rays' exit
+  // parameters min_b L_b / |n_b| non-decreasing (L: the node's upwind-frame
+  // coordinates, B along the face's axis; the ray leaves the block where the
+  // first of them reaches 0)
+  {
+    const int N1 = B + 1, NN = N1 * N1;
+    std::vector<uint16_t> no((size_t)3 * NN);
+    for (int i = 0; i < N; ++i) {
+      vet::geom::node_order<float>(T(i), B, no.data());
+      const double *dir = &d[4 * order[i]];
+      for (int a = 0; a < 3; ++a) {
+        std::vector<int> seen(NN, 0);
+        double prev = -1.0;
+        for (int k = 0; k < NN; ++k) {
+          const int r = no[(size_t)a * NN + k];
+          if (r >= NN || seen[r]++) return fail("node order is not a permutation of a face's nodes");
+          const int ub = r / N1, uc = r % N1;
+          const int L[3] = {a == 0 ? B : ub, a == 1 ? B : (a == 0 ? ub : uc), a == 2 ? B : uc};
+          double t = 1e300;
+          for (int b = 0; b < 3; ++b) t = std::min(t, L[b] / std::fabs(dir[b]));
+          if (t < prev - 1e-9) return fail("node order is not by ray length");
+          prev = t;
+        }
+      }
+    }
+  }
   const int nl = nb[0] + nb[1] + nb[2] - 2;
   for (int g : {1, 2, 4, 8}) {
     std::vector<int> off(nl + 1), poff(nl + 1);
