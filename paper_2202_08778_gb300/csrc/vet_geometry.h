@@ -395,11 +395,12 @@ inline bool mirrored_cell_pair(const unsigned char *ta, const unsigned char *tb,
 // Returns the number of items, or -1 if it exceeds `cap`.
 // Node order of the paired face pass for one template: for each face axis
 // a, the (B+1)^2 nodes (ub, uc) of a block's downwind face, as ub (B+1) + uc,
-// sorted by the index of their ray's exit event (ties by node index).  The
-// face pass hands consecutive entries to the lanes of a warp, which march in
-// lockstep for as many steps as their longest ray: in row order their rays
-// differ in length by up to a block edge's worth of events (0.59 of the
-// lane-steps useful on the 192-direction set), sorted they nearly agree.
+// by the index of their ray's exit event (ties by node index), each node at
+// most 31 places from its rank in that order.  The face pass hands
+// consecutive entries to the lanes of a warp, which march in lockstep for
+// as many steps as their longest ray: in row order their rays differ in
+// length by up to a block edge's worth of events (0.59 of the lane-steps
+// useful on the 192-direction set), in this order they nearly agree.
 template <typename R>
 inline void node_order(const unsigned char *tpl, int B, uint16_t *out) {
   const TplLayout L = tpl_layout<R>(B);
@@ -416,6 +417,45 @@ inline void node_order(const unsigned char *tpl, int B, uint16_t *out) {
       o[r] = (uint16_t)r;
     }
     std::stable_sort(o, o + NN, [&](uint16_t x, uint16_t y) { return last[x] < last[y]; });
+    // then spread the tile banks: a node ray's 16-byte tile entries sit at
+    // (c0 + c1 + c2) mod 8 of the 8 bank groups (the tile's strides are
+    // 1 mod 8), c its start cell, and eight lanes of a warp load in one
+    // wavefront only where their groups differ; each position takes the
+    // earliest of the next 32 nodes whose group differs from the 7 placed
+    // before it (else the earliest), which keeps the length order to within
+    // a few places
+    int sg[3];
+    {
+      const TplHead<R> *hd = reinterpret_cast<const TplHead<R> *>(tpl);
+      for (int b = 0; b < 3; ++b) sg[b] = hd->sgn[b];
+    }
+    std::vector<int> grp(NN);
+    for (int r = 0; r < NN; ++r) {
+      const int ub = r / N1, uc = r % N1;
+      const int Lq[3] = {a == 0 ? B : ub, a == 1 ? B : (a == 0 ? ub : uc), a == 2 ? B : uc};
+      int c = 0;
+      for (int b = 0; b < 3; ++b) c += sg[b] > 0 ? Lq[b] - 1 : B - Lq[b];
+      grp[r] = ((c % 8) + 8) % 8;
+    }
+    std::vector<uint16_t> sorted(o, o + NN);
+    std::vector<char> used(NN, 0);
+    int head = 0;
+    for (int p = 0; p < NN; ++p) {
+      while (head < NN && used[head]) ++head;
+      int pick = head;
+      for (int c = head; c < NN && c < head + 32; ++c) {
+        if (used[c]) continue;
+        bool distinct = true;
+        for (int k = 1; k <= 7 && k <= p; ++k)
+          if (grp[o[p - k]] == grp[sorted[c]]) distinct = false;
+        if (distinct) {
+          pick = c;
+          break;
+        }
+      }
+      used[pick] = 1;
+      o[p] = sorted[pick];
+    }
   }
 }
 
