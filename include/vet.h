@@ -421,8 +421,9 @@ vet_status vet_reuse_decision(const float *change, int age, int first, double to
  * f_aa <= 0 gives tau_c = inf and C's cell factor 0, kappa_R = 0 gives
  * tau_c = 0 and the correction 1.  FP32: below tau_c = 1/4 the correction
  * comes from the ray march's thin-segment cubic (no cancellation), above it
- * from the hardware exponential; quotients are fast (a few ulp), so the
- * result is within a few 1e-7 relative of the exact formula.
+ * from the hardware exponential; quotients use the hardware reciprocal (a
+ * few ulp), so the result is within a few 1e-7 relative of the exact
+ * formula.
  * grid: cells and h (block is ignored); f: [6][nz][ny][nx] as vet_closure
  * writes it (only component a is read); kappa_R: [nz][ny][nx], rho kappa_R
  * per unit length; c > 0; C_out: [nz][ny][nx+1] for a = 0, [nz][ny+1][nx]
