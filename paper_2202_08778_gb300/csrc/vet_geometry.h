@@ -384,6 +384,70 @@ inline bool mirrored_cell_pair(const unsigned char *ta, const unsigned char *tb,
   return mirror_templates<R>(ta, tb, B);
 }
 
+// Node order of the paired face pass for one template.  A node ray starts
+// on a block's downwind face normal to axis a, at node (ub, uc), code
+// a (B+1)^2 + ub (B+1) + uc.  The face pass hands consecutive entries of an
+// order to the lanes of a warp, which march in lockstep for as many steps
+// as their longest ray: in row order their rays differ in length by up to a
+// block edge's worth of events (0.59 of the lane-steps useful on the
+// 192-direction set).  out[a (B+1)^2 + k], a = 0..2: the face's nodes as
+// ub (B+1) + uc by the index of their ray's exit event (ties by node
+// index), each within 31 places of its rank in that order; then
+// out[3 (B+1)^2 + k]: the codes of all three faces merged the same way,
+// for items whose three downwind faces are all computed.
+template <typename R>
+inline void node_order(const unsigned char *tpl, int B, uint16_t *out) {
+  const TplLayout L = tpl_layout<R>(B);
+  const int16_t *npos = reinterpret_cast<const int16_t *>(tpl + L.npos);
+  const TplHead<R> *hd = reinterpret_cast<const TplHead<R> *>(tpl);
+  const int N1 = B + 1, NN = N1 * N1;
+  // exit event index and tile bank group of every node code: a ray's
+  // 16-byte tile entries sit in group (c0 + c1 + c2) mod 8 of the eight
+  // (the tile's strides are 1 mod 8), c its start cell, and eight lanes of
+  // a warp load in one wavefront only where their groups differ
+  std::vector<int> last(3 * NN), grp(3 * NN);
+  for (int a = 0; a < 3; ++a)
+    for (int r = 0; r < NN; ++r) {
+      const int ub = r / N1, uc = r % N1;
+      // upwind-frame node coordinates: B along the face's axis
+      const int Lq[3] = {a == 0 ? B : ub, a == 1 ? B : (a == 0 ? ub : uc), a == 2 ? B : uc};
+      last[a * NN + r] = std::min({(int)npos[Lq[0]], (int)npos[N1 + Lq[1]], (int)npos[2 * N1 + Lq[2]]});
+      int c = 0;
+      for (int b = 0; b < 3; ++b) c += hd->sgn[b] > 0 ? Lq[b] - 1 : B - Lq[b];
+      grp[a * NN + r] = ((c % 8) + 8) % 8;
+    }
+  // codes [c0, c0 + n) sorted by exit event, then each position takes the
+  // earliest of the next 32 whose group differs from the 7 placed before it
+  // (else the earliest), which keeps the length order to within a few places
+  auto order = [&](int c0, int n, uint16_t *o, int sub) {
+    std::vector<int> sorted(n);
+    for (int k = 0; k < n; ++k) sorted[k] = c0 + k;
+    std::stable_sort(sorted.begin(), sorted.end(), [&](int x, int y) { return last[x] < last[y]; });
+    std::vector<char> used(n, 0);
+    std::vector<int> placed(n);
+    int head = 0;
+    for (int p = 0; p < n; ++p) {
+      while (head < n && used[head]) ++head;
+      int pick = head;
+      for (int c = head; c < n && c < head + 32; ++c) {
+        if (used[c]) continue;
+        bool distinct = true;
+        for (int k = 1; k <= 7 && k <= p; ++k)
+          if (grp[placed[p - k]] == grp[sorted[c]]) distinct = false;
+        if (distinct) {
+          pick = c;
+          break;
+        }
+      }
+      used[pick] = 1;
+      placed[p] = sorted[pick];
+      o[p] = (uint16_t)(placed[p] - sub);
+    }
+  };
+  for (int a = 0; a < 3; ++a) order(a * NN, NN, out + a * NN, a * NN);
+  order(0, 3 * NN, out + 3 * NN, 0);
+}
+
 // Face-pass schedule: level L of block b in octant o is b's upwind-ordered
 // index sum; one item = (block, up to `group` directions of one octant), or
 // up to level_group[L] directions on level L when that table is given.
@@ -393,72 +457,6 @@ inline bool mirrored_cell_pair(const unsigned char *ta, const unsigned char *tb,
 // (the order of mirror_octant_order).
 // Writes level_off[0..nlevels] and, when items != nullptr, the items.
 // Returns the number of items, or -1 if it exceeds `cap`.
-// Node order of the paired face pass for one template: for each face axis
-// a, the (B+1)^2 nodes (ub, uc) of a block's downwind face, as ub (B+1) + uc,
-// by the index of their ray's exit event (ties by node index), each node at
-// most 31 places from its rank in that order.  The face pass hands
-// consecutive entries to the lanes of a warp, which march in lockstep for
-// as many steps as their longest ray: in row order their rays differ in
-// length by up to a block edge's worth of events (0.59 of the lane-steps
-// useful on the 192-direction set), in this order they nearly agree.
-template <typename R>
-inline void node_order(const unsigned char *tpl, int B, uint16_t *out) {
-  const TplLayout L = tpl_layout<R>(B);
-  const int16_t *npos = reinterpret_cast<const int16_t *>(tpl + L.npos);
-  const int N1 = B + 1, NN = N1 * N1;
-  std::vector<int> last(NN);
-  for (int a = 0; a < 3; ++a) {
-    uint16_t *o = out + a * NN;
-    for (int r = 0; r < NN; ++r) {
-      const int ub = r / N1, uc = r % N1;
-      // upwind-frame node coordinates: B along the face's axis
-      const int L0 = a == 0 ? B : ub, L1 = a == 1 ? B : (a == 0 ? ub : uc), L2 = a == 2 ? B : uc;
-      last[r] = std::min({(int)npos[L0], (int)npos[N1 + L1], (int)npos[2 * N1 + L2]});
-      o[r] = (uint16_t)r;
-    }
-    std::stable_sort(o, o + NN, [&](uint16_t x, uint16_t y) { return last[x] < last[y]; });
-    // then spread the tile banks: a node ray's 16-byte tile entries sit at
-    // (c0 + c1 + c2) mod 8 of the 8 bank groups (the tile's strides are
-    // 1 mod 8), c its start cell, and eight lanes of a warp load in one
-    // wavefront only where their groups differ; each position takes the
-    // earliest of the next 32 nodes whose group differs from the 7 placed
-    // before it (else the earliest), which keeps the length order to within
-    // a few places
-    int sg[3];
-    {
-      const TplHead<R> *hd = reinterpret_cast<const TplHead<R> *>(tpl);
-      for (int b = 0; b < 3; ++b) sg[b] = hd->sgn[b];
-    }
-    std::vector<int> grp(NN);
-    for (int r = 0; r < NN; ++r) {
-      const int ub = r / N1, uc = r % N1;
-      const int Lq[3] = {a == 0 ? B : ub, a == 1 ? B : (a == 0 ? ub : uc), a == 2 ? B : uc};
-      int c = 0;
-      for (int b = 0; b < 3; ++b) c += sg[b] > 0 ? Lq[b] - 1 : B - Lq[b];
-      grp[r] = ((c % 8) + 8) % 8;
-    }
-    std::vector<uint16_t> sorted(o, o + NN);
-    std::vector<char> used(NN, 0);
-    int head = 0;
-    for (int p = 0; p < NN; ++p) {
-      while (head < NN && used[head]) ++head;
-      int pick = head;
-      for (int c = head; c < NN && c < head + 32; ++c) {
-        if (used[c]) continue;
-        bool distinct = true;
-        for (int k = 1; k <= 7 && k <= p; ++k)
-          if (grp[o[p - k]] == grp[sorted[c]]) distinct = false;
-        if (distinct) {
-          pick = c;
-          break;
-        }
-      }
-      used[pick] = 1;
-      o[p] = sorted[pick];
-    }
-  }
-}
-
 inline long long build_schedule(const int nb[3], const int ob[9], int group, FaceItem *items, long long cap,
                                 int *level_off, const int *level_group = nullptr, bool paired = false) {
   const int nlevels = nb[0] + nb[1] + nb[2] - 2;

@@ -300,9 +300,9 @@ vet_status build_context(vet_ctx *c) {
     return cuda_err(c, e, "upload order");
   if (c->dims.face_paired) {
     const int NN = (B + 1) * (B + 1);
-    std::vector<uint16_t> nord((size_t)N * 3 * NN);
+    std::vector<uint16_t> nord((size_t)N * 6 * NN);
     for (int i = 0; i < N; ++i)
-      vet::geom::node_order<R>(tpl.data() + (size_t)i * tbytes, B, nord.data() + (size_t)i * 3 * NN);
+      vet::geom::node_order<R>(tpl.data() + (size_t)i * tbytes, B, nord.data() + (size_t)i * 6 * NN);
     if ((e = cudaMalloc((void **)&c->d_node_order, sizeof(uint16_t) * nord.size())))
       return cuda_err(c, e, "cudaMalloc(node order)");
     if ((e = cudaMemcpy(c->d_node_order, nord.data(), sizeof(uint16_t) * nord.size(), cudaMemcpyHostToDevice)))

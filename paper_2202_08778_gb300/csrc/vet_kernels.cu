@@ -1435,13 +1435,22 @@ __global__ void __launch_bounds__(kFaceThreads, 2)
     // incoming faces
     const uint32_t ps = slots_s + (uint32_t)(sb * j);
     const uint32_t f1 = ps + (uint32_t)TL.node_bytes, f2 = slots_s + (uint32_t)(sb * cnt + fb3 * j);
-    const int a = (live >> (2 * ai)) & 3;
-    // the k-th node of the face by ray length, every other face of the item
-    // taken from its longest ray down, so that a warp that straddles two
-    // faces joins rays of similar length too
-    const int r = g.node_order ? (int)__ldg(g.node_order + ((size_t)(it.dir_begin + j) * 3 + a) * NN +
-                                            ((q & 1) ? NN - 1 - k : k))
-                               : k;
+    // the k-th node ray by length: of the face, or where all three faces
+    // are computed, of the three merged; every other face (or direction)
+    // of the item taken from its longest ray down, so that a warp that
+    // straddles two joins rays of similar length too
+    int a = (live >> (2 * ai)) & 3, r = k;
+    if (g.node_order) {
+      const uint16_t *no = g.node_order + (size_t)(it.dir_begin + j) * (6 * NN);
+      if (nlive == 3) {
+        const int k3 = w - j * (3 * NN);
+        const int code = __ldg(no + 3 * NN + ((j & 1) ? 3 * NN - 1 - k3 : k3));
+        a = code / NN;
+        r = code - a * NN;
+      } else {
+        r = __ldg(no + a * NN + ((q & 1) ? NN - 1 - k : k));
+      }
+    }
     const int ub = r / N1, uc = r - ub * N1;
     const int L0 = a == 0 ? B : ub;
     const int L1 = a == 1 ? B : (a == 0 ? ub : uc);

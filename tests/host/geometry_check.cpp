@@ -6,9 +6,9 @@
 //  - the paired cell pass marches every antipodal pair of a rotated set as a
 //    mirrored pair, and never one with a zero direction component (whose
 //    sign the antipode keeps) of the unrotated set;
-//  - the paired face pass's node order is, per template and face axis, a
-//    permutation of the face's nodes within 31 places of their order by
-//    node-ray length;
+//  - the paired face pass's node orders (per template: each face axis, and
+//    the three faces merged) are permutations of the nodes within 31
+//    places of their order by node-ray length;
 //  - the paired face-pass schedule, with each item's point-mirrored block and
 //    antipodal directions added, lists every (block, direction) of the
 //    unpaired schedule exactly once, level by level.
@@ -101,32 +101,39 @@ int main(int argc, char **argv) {
       if (other != j && vet::geom::mirror_node_templates<float>(T(i), T(other), B))
         return fail("a non-antipodal pair passed the node mirror check");
     }
-  // the paired face pass's node order: per template and face axis a
-  // permutation of the (B+1)^2 face nodes, each node within 31 places of its
-  // rank by the node ray's exit parameter min_b L_b / |n_b| (L: the node's
-  // upwind-frame coordinates, B along the face's axis; the ray leaves the
-  // block where the first of them reaches 0)
+  // the paired face pass's node order: per template, for each face axis a
+  // permutation of the (B+1)^2 face nodes, then one of the codes of all
+  // three faces, each node within 31 places of its rank by the node ray's
+  // exit parameter min_b L_b / |n_b| (L: the node's upwind-frame
+  // coordinates, B along the face's axis; the ray leaves the block where
+  // the first of them reaches 0)
   {
     const int N1 = B + 1, NN = N1 * N1;
-    std::vector<uint16_t> no((size_t)3 * NN);
+    std::vector<uint16_t> no((size_t)6 * NN);
     for (int i = 0; i < N; ++i) {
       vet::geom::node_order<float>(T(i), B, no.data());
       const double *dir = &d[4 * order[i]];
-      for (int a = 0; a < 3; ++a) {
-        std::vector<double> t(NN), ts(NN);
-        for (int r = 0; r < NN; ++r) {
-          const int ub = r / N1, uc = r % N1;
-          const int L[3] = {a == 0 ? B : ub, a == 1 ? B : (a == 0 ? ub : uc), a == 2 ? B : uc};
-          t[r] = 1e300;
-          for (int b = 0; b < 3; ++b) t[r] = std::min(t[r], L[b] / std::fabs(dir[b]));
-        }
-        ts = t;
+      auto exit_t = [&](int code) {
+        const int a = code / NN, r = code % NN, ub = r / N1, uc = r % N1;
+        const int L[3] = {a == 0 ? B : ub, a == 1 ? B : (a == 0 ? ub : uc), a == 2 ? B : uc};
+        double t = 1e300;
+        for (int b = 0; b < 3; ++b) t = std::min(t, L[b] / std::fabs(dir[b]));
+        return t;
+      };
+      // (first code, count, offset of the list in no, value offset)
+      for (int part = 0; part < 4; ++part) {
+        const int c0 = part < 3 ? part * NN : 0, n = part < 3 ? NN : 3 * NN;
+        const uint16_t *o = no.data() + (part < 3 ? part * NN : 3 * NN);
+        std::vector<double> ts(n);
+        for (int k = 0; k < n; ++k) ts[k] = exit_t(c0 + k);
         std::sort(ts.begin(), ts.end());
-        std::vector<int> seen(NN, 0);
-        for (int k = 0; k < NN; ++k) {
-          const int r = no[(size_t)a * NN + k];
-          if (r >= NN || seen[r]++) return fail("node order is not a permutation of a face's nodes");
-          if (t[r] < ts[std::max(0, k - 31)] - 1e-9 || t[r] > ts[std::min(NN - 1, k + 31)] + 1e-9)
+        std::vector<int> seen(n, 0);
+        for (int k = 0; k < n; ++k) {
+          const int code = o[k] + (part < 3 ? c0 : 0);
+          if (code - c0 < 0 || code - c0 >= n || seen[code - c0]++)
+            return fail("node order is not a permutation of a face's nodes");
+          const double t = exit_t(code);
+          if (t < ts[std::max(0, k - 31)] - 1e-9 || t > ts[std::min(n - 1, k + 31)] + 1e-9)
             return fail("node order is not by ray length");
         }
       }
