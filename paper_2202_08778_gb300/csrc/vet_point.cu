@@ -15,7 +15,8 @@
 //
 // One thread per cell (grid-stride, x fastest): the rays of a warp start at
 // the same point and stay close, so their kappa reads are near one another
-// in the caches.  Geometry in cell units (planes at integers); every plane
+// in the caches; each thread walks four steps ahead of its sum of tau, so
+// that four reads are in flight.  Geometry in cell units (planes at integers); every plane
 // crossing is computed from the source position, not accumulated, so a
 // crossing's error is a few ulp of its own distance.  The walk crosses at
 // most |di| + |dj| + |dk| + 1 cells and is capped at nx + ny + nz + 3 steps.
@@ -67,28 +68,47 @@ __global__ void __launch_bounds__(256) point_kernel(PointArgs a, const float *__
     const float dr = t_out - t_in;
     // walk from the source cell to the entry of the target cell: the next
     // crossing of each axis is kept, and only the axis just crossed has its
-    // next crossing recomputed (from the source position, not accumulated)
-    int cur[3] = {(int)floorf(a.xs[0]), (int)floorf(a.xs[1]), (int)floorf(a.xs[2])};
-    const long long sstride[3] = {1, a.nx, (long long)a.nx * a.ny};
-    float tm[3];
-    int stp[3];
-    long long sidx[3];
-    for (int q = 0; q < 3; ++q) {
-      stp[q] = d[q] > 0.f ? 1 : -1;
-      sidx[q] = d[q] > 0.f ? sstride[q] : -sstride[q];
-      tm[q] = d[q] != 0.f ? (cur[q] + (d[q] > 0.f ? 1 : 0) - a.xs[q]) * inv[q] : INFINITY;
-    }
-    long long idx = ((long long)cur[2] * a.ny + cur[1]) * a.nx + cur[0];
+    // next crossing recomputed (from the source position, not accumulated).
+    // The per-axis state is kept in scalars updated by selects (an array
+    // indexed by the crossed axis would live in local memory), and the walk,
+    // which does not depend on kappa, runs four steps ahead of the sum of
+    // tau: their four kappa loads are in flight together, and tau takes them
+    // in order (a step past the end or outside the grid adds 0 times 0).
+    int c0 = (int)floorf(a.xs[0]), c1 = (int)floorf(a.xs[1]), c2 = (int)floorf(a.xs[2]);
+    const int s0 = d[0] > 0.f ? 1 : -1, s1 = d[1] > 0.f ? 1 : -1, s2 = d[2] > 0.f ? 1 : -1;
+    const int o0 = d[0] > 0.f ? 1 : 0, o1 = d[1] > 0.f ? 1 : 0, o2 = d[2] > 0.f ? 1 : 0;
+    const long long plane = (long long)a.nx * a.ny;
+    const long long e0 = s0, e1 = s1 > 0 ? (long long)a.nx : -(long long)a.nx, e2 = s2 > 0 ? plane : -plane;
+    float tm0 = d[0] != 0.f ? (c0 + o0 - a.xs[0]) * inv[0] : INFINITY;
+    float tm1 = d[1] != 0.f ? (c1 + o1 - a.xs[1]) * inv[1] : INFINITY;
+    float tm2 = d[2] != 0.f ? (c2 + o2 - a.xs[2]) * inv[2] : INFINITY;
+    long long idx = ((long long)c2 * a.ny + c1) * a.nx + c0;
     float t = 0.f, tau = 0.f;
-    for (int s = 0; s < cap && t < t_in - 1e-5f; ++s) {
-      const int ax = tm[0] <= tm[1] ? (tm[0] <= tm[2] ? 0 : 2) : (tm[1] <= tm[2] ? 1 : 2);
-      const float tn = fminf(tm[ax], t_in);
-      if ((unsigned)cur[0] < (unsigned)a.nx && (unsigned)cur[1] < (unsigned)a.ny && (unsigned)cur[2] < (unsigned)a.nz)
-        tau = fmaf(kappa[idx], tn - t, tau);
-      t = tn;
-      cur[ax] += stp[ax];
-      idx += sidx[ax];
-      tm[ax] = (cur[ax] + (stp[ax] > 0 ? 1 : 0) - a.xs[ax]) * inv[ax];
+    for (int s = 0; s < cap && t < t_in - 1e-5f;) {
+      float kv[4], len[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool live = s < cap && t < t_in - 1e-5f;
+        const int ax = tm0 <= tm1 ? (tm0 <= tm2 ? 0 : 2) : (tm1 <= tm2 ? 1 : 2);
+        const float tn = fminf(ax == 0 ? tm0 : (ax == 1 ? tm1 : tm2), t_in);
+        const bool in = live && (unsigned)c0 < (unsigned)a.nx && (unsigned)c1 < (unsigned)a.ny &&
+                        (unsigned)c2 < (unsigned)a.nz;
+        kv[u] = in ? __ldg(kappa + idx) : 0.f;
+        len[u] = in ? tn - t : 0.f;
+        if (live) {
+          t = tn;
+          c0 += ax == 0 ? s0 : 0;
+          c1 += ax == 1 ? s1 : 0;
+          c2 += ax == 2 ? s2 : 0;
+          idx += ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+          if (ax == 0) tm0 = (c0 + o0 - a.xs[0]) * inv[0];
+          if (ax == 1) tm1 = (c1 + o1 - a.xs[1]) * inv[1];
+          if (ax == 2) tm2 = (c2 + o2 - a.xs[2]) * inv[2];
+          ++s;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) tau = fmaf(kv[u], len[u], tau);
     }
     const float taus = tau * a.h, drl = dr * a.h, rl = r * a.h;
     const float tc = kappa[c] * drl;
