@@ -298,7 +298,7 @@ vet_status build_context(vet_ctx *c) {
   if ((e = cudaMalloc((void **)&c->d_cell_order, sizeof(int) * N))) return cuda_err(c, e, "cudaMalloc(order)");
   if ((e = cudaMemcpy(c->d_cell_order, cell_order.data(), sizeof(int) * N, cudaMemcpyHostToDevice)))
     return cuda_err(c, e, "upload order");
-  if (c->dims.face_paired) {
+  {  // both face passes hand their node rays to the lanes by ray length
     const int NN = (B + 1) * (B + 1);
     std::vector<uint16_t> nord((size_t)N * 6 * NN);
     for (int i = 0; i < N; ++i)

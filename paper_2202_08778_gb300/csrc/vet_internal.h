@@ -119,10 +119,10 @@ struct GridDims {
   int dir_tile;       // directions per cell-pass tile (0: default)
   int paired;         // 1: the cell order lists antipodal pairs (d, -d), see the paired cell pass
   int face_paired;    // 1: face-pass items are mirrored block pairs, see the paired face pass
-  // paired face pass: per template (internal order), the (B+1)^2 face
-  // nodes of each face axis by ascending node-ray length, then the node
-  // codes of all three faces merged the same way, [N][6][(B+1)^2]
-  // (geom::node_order; null: row order)
+  // face passes: per template (internal order), the (B+1)^2 face nodes of
+  // each face axis by ascending node-ray length, then the node codes of all
+  // three faces merged the same way, [N][6][(B+1)^2] (geom::node_order;
+  // null: row order)
   const uint16_t *node_order;
 };
 

@@ -420,12 +420,24 @@ __global__ void __launch_bounds__(kFaceThreads, 3)
     // w = (j * nlive + ai) * NN + r; NN is a compile-time constant for a
     // templated block edge, and q / nlive (q < 3 * kMaxTune, nlive <= 3) is
     // a multiply-shift instead of a runtime division
-    const int q = w / NN, r = w - q * NN;
+    const int q = w / NN, k = w - q * NN;
     const int j = nlive == 1 ? q : (nlive == 2 ? q >> 1 : (q * 21846) >> 16);
     const int ai = q - j * nlive;
     const Tpl<R> T(slots + sb * j, TL);
     const R *fin = reinterpret_cast<const R *>(slots + sb * j + TL.node_bytes);
-    const int a = (live >> (2 * ai)) & 3;
+    // the k-th node ray by length, as in the paired face pass
+    int a = (live >> (2 * ai)) & 3, r = k;
+    if (g.node_order) {
+      const uint16_t *no = g.node_order + (size_t)(it.dir_begin + j) * (6 * NN);
+      if (nlive == 3) {
+        const int k3 = w - j * (3 * NN);
+        const int code = __ldg(no + 3 * NN + ((j & 1) ? 3 * NN - 1 - k3 : k3));
+        a = code / NN;
+        r = code - a * NN;
+      } else {
+        r = __ldg(no + a * NN + ((q & 1) ? NN - 1 - k : k));
+      }
+    }
     const int ub = r / N1, uc = r - ub * N1;  // upwind-frame node on the downwind face of axis a
     // upwind-frame node coordinates (L0, L1, L2): B along the face's axis
     const int L0 = a == 0 ? B : ub;
