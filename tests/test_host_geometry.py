@@ -1,7 +1,8 @@
 """Host logic of the mirrored-pair passes (vet_geometry.h), compiled with the
 host C++ compiler and run without a GPU: antipodes at equal positions of
-opposite octants, the cell- and node-ray mirror checks, and the paired
-face-pass schedule covering the unpaired one level by level."""
+opposite octants, the cell- and node-ray mirror checks, the face passes'
+node order by ray length, and the paired face-pass schedule covering the
+unpaired one level by level."""
 import os
 import shutil
 import subprocess
@@ -32,7 +33,9 @@ def checker(tmp_path_factory):
 
 
 @pytest.mark.parametrize("nb,B,nside", [((8, 8, 8), 16, 4), ((4, 2, 3), 8, 2), ((3, 3, 3), 16, 2), ((1, 1, 1), 8, 1),
-                                        ((5, 2, 1), 16, 4), ((2, 2, 2), 8, 8)])
+                                        ((5, 2, 1), 16, 4), ((2, 2, 2), 8, 8),
+                                        # block edges of the unpaired passes (templates, node order, schedule)
+                                        ((3, 2, 2), 12, 2), ((2, 2, 2), 32, 2)])
 def test_mirrored_pairs_and_paired_schedule(checker, nb, B, nside):
     r = subprocess.run([checker, *map(str, nb), str(B), str(nside)], capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
